@@ -1,0 +1,539 @@
+"""Plain FP64 CPU oracle of the PDE-EPDiff LDDMM hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and the CPU-baseline / reference legs of ``bench.py`` may import it.  It
+shares no code with the CUDA path and imports nothing from the package.
+
+What it computes (Hernandez, "PDE-constrained LDDMM via geodesic shooting
+and inexact Gauss-Newton-Krylov optimization using the incremental adjoint
+Jacobi equations", arXiv 1807.04638):
+
+* the metric ``L = (Id - alpha Lap)^s`` and ``K = L^-1`` (Sec. 2.1),
+* the EPDiff right-hand side ``dv/dt = -K ad*_v L v`` with
+  ``ad*_v m = (Dv)^T m + (Dm) v + m div v`` (Sec. 2.2, the EPDiff equation),
+* geodesic shooting of ``v0`` and transport of the source image,
+  ``m(1) = I0 o (phi_1)^-1`` (Sec. 3, state equation),
+* the energy ``E(v0) = w <L v0, v0> + ||m(1) - I1||^2`` (Sec. 3; ``w`` plays
+  the role of ``sigma^2``),
+* the reduced gradient: ``grad_{v1} E = lambda(1) grad m(1)`` with
+  ``lambda(1) = -2 (m(1) - I1)``, carried back to ``t = 0`` by the adjoint
+  Jacobi equations (Sec. 2.2 and Sec. 3),
+* the Gauss-Newton Hessian-vector product: incremental EPDiff forward, the
+  Gauss-Newton source ``delta lambda(1) grad m(1)`` with
+  ``delta lambda(1) = -2 delta m(1)``, carried back by the same adjoint sweep
+  (Sec. 3, with the paper's Gauss-Newton drops),
+* PCG with preconditioner ``K`` on ``H dv0 = -grad E`` and the Gauss-Newton
+  update of ``v0`` (Sec. 2.3 and Sec. 3), plus the reporting metrics of
+  Sec. 4 (relative MSE, relative gradient sup-norm, Jacobian determinant).
+
+Discretisation choices where the paper is silent (each restated where used):
+pseudo-spectral derivatives on a periodic grid with the Nyquist mode of first
+derivatives zeroed; Heun time stepping of the shooting and of the augmented
+Jacobi system; the backward sweep is the exact discrete transpose of the
+forward tangent sweep; semi-Lagrangian transport of the inverse-map
+displacement with a Heun backward characteristic; Catmull-Rom (Keys, a=-1/2)
+or trilinear periodic interpolation.
+
+Layout: scalar fields ``[n0, n1, n2]``; vector fields ``[3, n0, n1, n2]``;
+component ``c`` of a vector field is its displacement / velocity along axis
+``c``.  Inner products ``<f, g> = h0 h1 h2 sum_x sum_c f_c g_c``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, List, Optional
+
+import numpy as np
+
+AXES = (-3, -2, -1)
+
+
+# ---------------------------------------------------------------------------
+# Grid, symbols and spectral operators (Sec. 2.1: L = (Id - alpha Lap)^s)
+# ---------------------------------------------------------------------------
+
+class Grid:
+    """Periodic grid with spectral symbols.
+
+    ``kappa_a = (2 pi / l_a) k_a`` with integer ``k_a`` in FFT order.  The
+    first-derivative symbol ``i kappa_a`` has its Nyquist entry zeroed (so the
+    discrete derivative is real and exactly skew-symmetric); ``|kappa|^2``
+    keeps the Nyquist entry.  ``L_hat = (1 + alpha |kappa|^2)^s``.
+    """
+
+    def __init__(self, n, alpha=0.01, s=2, lengths=None):
+        self.n = tuple(int(x) for x in n)
+        self.lengths = tuple(float(x) for x in lengths) if lengths is not None else (2 * math.pi,) * 3
+        self.h = tuple(l / m for l, m in zip(self.lengths, self.n))
+        self.alpha = float(alpha)
+        self.s = int(s)
+        self.cell = self.h[0] * self.h[1] * self.h[2]
+        k = [np.fft.fftfreq(self.n[0]) * self.n[0],
+             np.fft.fftfreq(self.n[1]) * self.n[1],
+             np.fft.rfftfreq(self.n[2]) * self.n[2]]
+        kap = [2 * math.pi / self.lengths[a] * k[a] for a in range(3)]
+        dsym = []
+        for a in range(3):
+            d = kap[a].copy()
+            if self.n[a] % 2 == 0:
+                d[np.abs(k[a]) == self.n[a] // 2] = 0.0
+            dsym.append(d)
+        shp = [(-1, 1, 1), (1, -1, 1), (1, 1, -1)]
+        self.ik = [1j * dsym[a].reshape(shp[a]) for a in range(3)]
+        ksq = sum(kap[a].reshape(shp[a]) ** 2 for a in range(3))
+        self.ksq = ksq
+        self.Lhat = (1.0 + self.alpha * ksq) ** self.s
+        self.Khat = 1.0 / self.Lhat
+        self.coords = np.stack(np.meshgrid(*[np.arange(m, dtype=np.float64) for m in self.n],
+                                           indexing="ij"))
+
+    # transforms --------------------------------------------------------
+    def fwd(self, f):
+        return np.fft.rfftn(f, axes=AXES)
+
+    def inv(self, F):
+        return np.fft.irfftn(F, s=self.n, axes=AXES)
+
+    # operators on real fields -----------------------------------------
+    def D(self, f, j):
+        """Spectral first derivative along axis j (acts on the last 3 axes)."""
+        return self.inv(self.ik[j] * self.fwd(f))
+
+    def grad(self, f):
+        F = self.fwd(f)
+        return np.stack([self.inv(self.ik[j] * F) for j in range(3)])
+
+    def jac(self, v):
+        """J[i, j] = D_j v_i."""
+        V = self.fwd(v)
+        return np.stack([np.stack([self.inv(self.ik[j] * V[i]) for j in range(3)]) for i in range(3)])
+
+    def div(self, v):
+        V = self.fwd(v)
+        return self.inv(sum(self.ik[j] * V[j] for j in range(3)))
+
+    def L(self, v):
+        return self.inv(self.Lhat * self.fwd(v))
+
+    def K(self, v):
+        return self.inv(self.Khat * self.fwd(v))
+
+    def dot(self, f, g):
+        return float(self.cell * np.sum(np.asarray(f) * np.asarray(g)))
+
+
+# ---------------------------------------------------------------------------
+# ad* and ad (Sec. 2.2, EPDiff equation) and their exact discrete transposes
+# ---------------------------------------------------------------------------
+
+def ad_star(g: Grid, v, m):
+    """ad*_v m = (Dv)^T m + (Dm) v + m div v  (the bracket in the EPDiff equation).
+
+    [(Dv)^T m]_i = sum_j (D_i v_j) m_j ;  [(Dm) v]_i = sum_j (D_j m_i) v_j.
+    """
+    Jv = g.jac(v)
+    Jm = g.jac(m)
+    divv = Jv[0, 0] + Jv[1, 1] + Jv[2, 2]
+    out = np.empty_like(v)
+    for i in range(3):
+        out[i] = (sum(Jv[j, i] * m[j] for j in range(3))
+                  + sum(Jm[i, j] * v[j] for j in range(3))
+                  + m[i] * divv)
+    return out
+
+
+def ad(g: Grid, v, w):
+    """ad_v w = (Dv) w - (Dw) v, the L2-dual of ad*_v (continuum identity
+    <ad*_v m, w> = <m, ad_v w>)."""
+    Jv = g.jac(v)
+    Jw = g.jac(w)
+    out = np.empty_like(v)
+    for i in range(3):
+        out[i] = sum(Jv[i, j] * w[j] - Jw[i, j] * v[j] for j in range(3))
+    return out
+
+
+def ad_star_T_first(g: Grid, m, y):
+    """Exact grid transpose of eta -> ad*_eta m, applied to y.
+
+    [.]_j = -sum_i D_i(m_j y_i) + sum_i (D_j m_i) y_i - D_j(m . y).
+    """
+    Jm = g.jac(m)
+    my = sum(m[i] * y[i] for i in range(3))
+    gmy = g.grad(my)
+    out = np.empty_like(y)
+    for j in range(3):
+        out[j] = (-g.div(np.stack([m[j] * y[i] for i in range(3)]))
+                  + sum(Jm[i, j] * y[i] for i in range(3))
+                  - gmy[j])
+    return out
+
+
+def ad_star_T_second(g: Grid, v, y):
+    """Exact grid transpose of mu -> ad*_v mu, applied to y.
+
+    [.]_k = sum_i (D_i v_k) y_i - sum_j D_j(v_j y_k) + (div v) y_k.
+    """
+    Jv = g.jac(v)
+    divv = Jv[0, 0] + Jv[1, 1] + Jv[2, 2]
+    out = np.empty_like(y)
+    for k in range(3):
+        out[k] = (sum(Jv[k, i] * y[i] for i in range(3))
+                  - g.div(np.stack([v[j] * y[k] for j in range(3)]))
+                  + divv * y[k])
+    return out
+
+
+def ad_T(g: Grid, v, y):
+    """Exact grid transpose of xi -> ad_v xi, applied to y.
+
+    [.]_k = sum_i (D_k v_i) y_i + sum_j D_j(v_j y_k).
+    """
+    Jv = g.jac(v)
+    out = np.empty_like(y)
+    for k in range(3):
+        out[k] = (sum(Jv[i, k] * y[i] for i in range(3))
+                  + g.div(np.stack([v[j] * y[k] for j in range(3)])))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# EPDiff right-hand side and its linearisation (Sec. 2.2; Sec. 3 incremental
+# EPDiff equation)
+# ---------------------------------------------------------------------------
+
+def epdiff_rhs(g: Grid, v):
+    """R(v) = -K ad*_v (L v)."""
+    return -g.K(ad_star(g, v, g.L(v)))
+
+
+def epdiff_rhs_lin(g: Grid, v, eta):
+    """R'(v) eta = -K [ad*_eta (L v) + ad*_v (L eta)]  (incremental EPDiff:
+    d/dt dv = -(ad^dagger_dv v + ad^dagger_v dv))."""
+    return -g.K(ad_star(g, eta, g.L(v)) + ad_star(g, v, g.L(eta)))
+
+
+def epdiff_rhs_lin_T(g: Grid, v, y):
+    """Exact grid transpose of eta -> R'(v) eta."""
+    Ky = g.K(y)
+    return -(ad_star_T_first(g, g.L(v), Ky) + g.L(ad_star_T_second(g, v, Ky)))
+
+
+# ---------------------------------------------------------------------------
+# Periodic interpolation and semi-Lagrangian map transport (Sec. 3 state
+# equation  dm/dt + grad m . v = 0, solved through the inverse map)
+# ---------------------------------------------------------------------------
+
+def _catmull_rom_weights(t):
+    t2 = t * t
+    t3 = t2 * t
+    return [0.5 * (-t3 + 2 * t2 - t),
+            0.5 * (3 * t3 - 5 * t2 + 2),
+            0.5 * (-3 * t3 + 4 * t2 + t),
+            0.5 * (t3 - t2)]
+
+
+def interp(f, p, kind="cubic"):
+    """Periodic interpolation of samples ``f`` (last 3 axes) at voxel
+    coordinates ``p`` (shape [3, ...]).  ``kind`` = 'cubic' (Catmull-Rom,
+    Keys a=-1/2, taps -1..2) or 'linear' (trilinear, taps 0..1)."""
+    f = np.asarray(f)
+    n = f.shape[-3:]
+    base = np.floor(p)
+    t = p - base
+    base = base.astype(np.int64)
+    if kind == "cubic":
+        offs = (-1, 0, 1, 2)
+        w = [_catmull_rom_weights(t[a]) for a in range(3)]
+    elif kind == "linear":
+        offs = (0, 1)
+        w = [[1.0 - t[a], t[a]] for a in range(3)]
+    else:
+        raise ValueError(kind)
+    lead = f.shape[:-3]
+    out = np.zeros(lead + p.shape[1:])
+    for a0, o0 in enumerate(offs):
+        i0 = np.mod(base[0] + o0, n[0])
+        for a1, o1 in enumerate(offs):
+            i1 = np.mod(base[1] + o1, n[1])
+            w01 = w[0][a0] * w[1][a1]
+            for a2, o2 in enumerate(offs):
+                i2 = np.mod(base[2] + o2, n[2])
+                out += (w01 * w[2][a2]) * f[..., i0, i1, i2]
+    return out
+
+
+def sl_map_step(g: Grid, u_k, v_k, v_k1, dt, kind="cubic"):
+    """One semi-Lagrangian step of the inverse-map displacement u
+    (psi_t = x + u_t = phi_t^-1), Heun backward characteristic:
+
+      Xt = x - dt v_{k+1}(x);   X = x - dt/2 (v_{k+1}(x) + v_k(Xt));
+      u_{k+1}(x) = (X - x) + u_k(X).
+    """
+    h = np.array(g.h).reshape(3, 1, 1, 1)
+    x = g.coords
+    p1 = x - dt * v_k1 / h
+    vt = interp(v_k, p1, kind)
+    disp = -0.5 * dt * (v_k1 + vt)
+    return disp + interp(u_k, x + disp / h, kind)
+
+
+def warp(g: Grid, img, u, kind="cubic"):
+    """m(x) = I(x + u(x))."""
+    h = np.array(g.h).reshape(3, 1, 1, 1)
+    return interp(img, g.coords + u / h, kind)
+
+
+# ---------------------------------------------------------------------------
+# Geodesic shooting (Heun) with map transport
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Trajectory:
+    nt: int
+    v: List[np.ndarray]        # v_k, k = 0..nt
+    vstar: List[np.ndarray]    # Heun predictors v*_k, k = 0..nt-1
+    u: np.ndarray              # inverse-map displacement at t = 1
+    kinetic: List[float]       # <L v_k, v_k>, k = 0..nt
+    m1: Optional[np.ndarray] = None
+    grad_m1: Optional[np.ndarray] = None
+
+
+def shoot(g: Grid, v0, nt, I0=None, kind="cubic"):
+    """Forward geodesic shooting of v0 by Heun steps of the EPDiff equation,
+    with SL transport of the inverse map and the final warp m(1) = I0(x+u)."""
+    dt = 1.0 / nt
+    v = [np.array(v0, dtype=np.float64)]
+    vstar = []
+    u = np.zeros_like(v[0])
+    for k in range(nt):
+        r1 = epdiff_rhs(g, v[k])
+        vs = v[k] + dt * r1
+        r2 = epdiff_rhs(g, vs)
+        v.append(v[k] + 0.5 * dt * (r1 + r2))
+        vstar.append(vs)
+        u = sl_map_step(g, u, v[k], v[k + 1], dt, kind)
+    kin = [g.dot(g.L(vk), vk) for vk in v]
+    tr = Trajectory(nt=nt, v=v, vstar=vstar, u=u, kinetic=kin)
+    if I0 is not None:
+        tr.m1 = warp(g, I0, u, kind)
+        tr.grad_m1 = g.grad(tr.m1)
+    return tr
+
+
+# ---------------------------------------------------------------------------
+# Jacobi sweeps: forward tangent T and its exact transpose T^T
+# (Sec. 3: incremental EPDiff forward; adjoint / incremental adjoint Jacobi
+# field equations backward)
+# ---------------------------------------------------------------------------
+
+def jacobi_A(g: Grid, v, eta, xi):
+    """A_v(eta, xi) = (R'(v) eta, eta + ad_v xi); the Jacobi field equation
+    xi' = eta + ad_v xi is the right-trivialised variation of the flow."""
+    return epdiff_rhs_lin(g, v, eta), eta + ad(g, v, xi)
+
+
+def jacobi_A_T(g: Grid, v, yeta, yxi):
+    """Exact grid transpose of jacobi_A."""
+    return epdiff_rhs_lin_T(g, v, yeta) + yxi, ad_T(g, v, yxi)
+
+
+def tangent(g: Grid, tr: Trajectory, delta):
+    """T: delta v0 -> (eta_nt, xi_nt), Heun on the augmented system reusing the
+    stored states (v_k for stage 1, v*_k for stage 2)."""
+    dt = 1.0 / tr.nt
+    eta = np.array(delta, dtype=np.float64)
+    xi = np.zeros_like(eta)
+    for k in range(tr.nt):
+        be, bx = jacobi_A(g, tr.v[k], eta, xi)
+        es, xs = eta + dt * be, xi + dt * bx
+        ce, cx = jacobi_A(g, tr.vstar[k], es, xs)
+        eta = eta + 0.5 * dt * (be + ce)
+        xi = xi + 0.5 * dt * (bx + cx)
+    return eta, xi
+
+
+def adjoint(g: Grid, tr: Trajectory, b_xi, b_eta=None):
+    """T^T: exact transpose of ``tangent``.  Given the cotangent (b_eta, b_xi)
+    on (eta_nt, xi_nt), returns the cotangent on delta v0.
+
+    Per step (reverse order), with z' = z + dt/2 A z + dt/2 A*(z + dt A z):
+      a = A*^T zbar;  zbar <- zbar + dt/2 a + A^T (dt/2 zbar + dt^2/2 a).
+    """
+    dt = 1.0 / tr.nt
+    yx = np.array(b_xi, dtype=np.float64)
+    ye = np.zeros_like(yx) if b_eta is None else np.array(b_eta, dtype=np.float64)
+    for k in reversed(range(tr.nt)):
+        ae, ax = jacobi_A_T(g, tr.vstar[k], ye, yx)
+        te, tx = jacobi_A_T(g, tr.v[k], 0.5 * dt * ye + 0.5 * dt * dt * ae,
+                            0.5 * dt * yx + 0.5 * dt * dt * ax)
+        ye = ye + 0.5 * dt * ae + te
+        yx = yx + 0.5 * dt * ax + tx
+    return ye
+
+
+# ---------------------------------------------------------------------------
+# Energy, gradient, Gauss-Newton Hessian-vector product (Sec. 3)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Params:
+    alpha: float = 0.01
+    s: int = 2
+    weight: float = 1e-3       # w = sigma^2: E = w <L v0, v0> + ||m1 - I1||^2
+    nt: int = 10
+    interp: str = "cubic"
+    space: str = "V"           # 'V' or 'L2'
+
+
+def energy(g: Grid, p: Params, v0, I0, I1, tr=None):
+    """E(v0) = w <L v0, v0> + ||m(1) - I1||^2; returns (E, data, reg, tr)."""
+    if tr is None:
+        tr = shoot(g, v0, p.nt, I0, p.interp)
+    r = tr.m1 - I1
+    data = g.dot(r, r)
+    reg = p.weight * tr.kinetic[0]
+    return data + reg, data, reg, tr
+
+
+def gradient(g: Grid, p: Params, v0, I0, I1):
+    """Reduced L2 gradient  g = 2 w L v0 + T^T b,  b = lambda(1) grad m(1),
+    lambda(1) = -2 (m(1) - I1).  Returns (g_L2, E, data, reg, tr)."""
+    E, data, reg, tr = energy(g, p, v0, I0, I1)
+    b = -2.0 * (tr.m1 - I1)[None] * tr.grad_m1
+    gl2 = 2.0 * p.weight * g.L(v0) + adjoint(g, tr, b)
+    return gl2, E, data, reg, tr
+
+
+def hessvec(g: Grid, p: Params, tr: Trajectory, dv0):
+    """Gauss-Newton L2 Hessian-vector product at the trajectory tr:
+
+      H dv0 = 2 w L dv0 + T^T c,  with  delta m(1) = -grad m(1) . xi(1),
+      delta lambda(1) = -2 delta m(1)  and the Gauss-Newton source
+      c = delta lambda(1) grad m(1) = 2 (grad m(1) . xi(1)) grad m(1)
+      (the lambda(1) grad delta m(1) term is dropped).
+    """
+    _, xi = tangent(g, tr, dv0)
+    dm1 = -np.sum(tr.grad_m1 * xi, axis=0)
+    c = -2.0 * dm1[None] * tr.grad_m1
+    return 2.0 * p.weight * g.L(dv0) + adjoint(g, tr, c)
+
+
+def to_space(g: Grid, p: Params, f):
+    """Metric of the returned gradient / Hessian product: V -> K f, L2 -> f."""
+    return g.K(f) if p.space == "V" else f
+
+
+# ---------------------------------------------------------------------------
+# PCG and the Gauss-Newton-Krylov loop (Sec. 2.3 / Sec. 3)
+# ---------------------------------------------------------------------------
+
+def pcg(g: Grid, hmul: Callable, rhs, precond: Callable, maxit, rtol, space="V",
+        force_iters=None):
+    """PCG on H x = rhs with preconditioner K, x0 = 0.
+
+    Stopping norm relative to iteration 0: V -> sqrt(<r, K r>), L2 -> ||r||.
+    Stops early when <p, H p> <= 0.  ``force_iters`` replays a given iteration
+    count instead of the stopping test.  Returns (x, iterations).
+    """
+    x = np.zeros_like(rhs)
+    r = np.array(rhs, dtype=np.float64)
+    z = precond(r)
+    pdir = z.copy()
+    rz = g.dot(r, z)
+    norm0 = math.sqrt(max(rz, 0.0)) if space == "V" else math.sqrt(g.dot(r, r))
+    it = 0
+    limit = maxit if force_iters is None else force_iters
+    while it < limit:
+        q = hmul(pdir)
+        pq = g.dot(pdir, q)
+        if pq <= 0.0:
+            break
+        alpha = rz / pq
+        x = x + alpha * pdir
+        r = r - alpha * q
+        z = precond(r)
+        rz_new = g.dot(r, z)
+        it += 1
+        res = math.sqrt(max(rz_new, 0.0)) if space == "V" else math.sqrt(g.dot(r, r))
+        if force_iters is None and res <= rtol * norm0:
+            break
+        beta = rz_new / rz
+        pdir = z + beta * pdir
+        rz = rz_new
+    return x, it
+
+
+@dataclasses.dataclass
+class GNReport:
+    energies: List[float]
+    pcg_iters: List[int]
+    steps: List[float]
+    gnorm_rel: float
+    mse_rel: float
+    jac_min: float
+    jac_max: float
+    v0: np.ndarray
+
+
+def jacobian_det(g: Grid, u):
+    """det(I + D u) of the inverse map psi = x + u (spectral derivatives)."""
+    J = g.jac(u)
+    a = J + np.eye(3).reshape(3, 3, 1, 1, 1)
+    return (a[0, 0] * (a[1, 1] * a[2, 2] - a[1, 2] * a[2, 1])
+            - a[0, 1] * (a[1, 0] * a[2, 2] - a[1, 2] * a[2, 0])
+            + a[0, 2] * (a[1, 0] * a[2, 1] - a[1, 1] * a[2, 0]))
+
+
+def register(g: Grid, p: Params, I0, I1, v0=None, gn_maxit=5, pcg_maxit=10, pcg_rtol=0.1,
+             c1=1e-4, ls_maxit=10, replay=None):
+    """Inexact Gauss-Newton-Krylov registration in the space of initial
+    velocities.  Update v0 <- v0 + eps dv0 with H dv0 = -g (the descent sign;
+    the paper writes the update with the opposite sign convention on dv0),
+    Armijo backtracking from eps = 1 with halving.
+
+    ``replay`` = list of (pcg_iterations, eps) per GN iteration forces the
+    decisions (used to compare trajectories computed at another precision).
+    """
+    v = np.zeros((3,) + g.n) if v0 is None else np.array(v0, dtype=np.float64)
+    energies, iters, steps = [], [], []
+    g0max = None
+    gmax = None
+    for n_it in range(gn_maxit):
+        gl2, E, _, _, tr = gradient(g, p, v, I0, I1)
+        gsp = to_space(g, p, gl2)
+        gmax = float(np.abs(gsp).max())
+        if g0max is None:
+            g0max = gmax
+        energies.append(E)
+        forced = replay[n_it] if replay is not None else None
+        x, it = pcg(g, lambda d: hessvec(g, p, tr, d), -gl2, g.K, pcg_maxit, pcg_rtol,
+                    p.space, force_iters=None if forced is None else forced[0])
+        iters.append(it)
+        slope = g.dot(gl2, x)
+        if forced is not None:
+            eps = forced[1]
+        else:
+            eps = 1.0
+            accepted = False
+            for _ in range(ls_maxit):
+                Et = energy(g, p, v + eps * x, I0, I1)[0]
+                if Et <= E + c1 * eps * slope:
+                    accepted = True
+                    break
+                eps *= 0.5
+            if not accepted:
+                eps = 0.0
+        steps.append(eps)
+        if eps == 0.0:
+            break
+        v = v + eps * x
+    Ef, _, _, trf = energy(g, p, v, I0, I1)
+    energies.append(Ef)
+    gl2f = gradient(g, p, v, I0, I1)[0]
+    gnorm_rel = float(np.abs(to_space(g, p, gl2f)).max() / g0max) if g0max else 0.0
+    mse = g.dot(trf.m1 - I1, trf.m1 - I1) / g.dot(I0 - I1, I0 - I1)
+    J = jacobian_det(g, trf.u)
+    return GNReport(energies=energies, pcg_iters=iters, steps=steps, gnorm_rel=gnorm_rel,
+                    mse_rel=float(mse), jac_min=float(J.min()), jac_max=float(J.max()), v0=v)
