@@ -1,0 +1,103 @@
+// Shared device-side definitions: complex type, spectral symbols, pass jobs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lddmm {
+
+template <class T> struct cpx;
+template <> struct __align__(8) cpx<float> { float x, y; };
+template <> struct __align__(16) cpx<double> { double x, y; };
+
+template <class T> __host__ __device__ __forceinline__ cpx<T> mk(T a, T b) { cpx<T> r; r.x = a; r.y = b; return r; }
+template <class T> __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <class T> __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <class T> __device__ __forceinline__ cpx<T> operator*(cpx<T> a, cpx<T> b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <class T> __device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) { return mk(s * a.x, s * a.y); }
+template <class T> __device__ __forceinline__ cpx<T> cj(cpx<T> a) { return mk(a.x, -a.y); }
+__device__ __forceinline__ cpx<float> ldg(const cpx<float>* p) {
+    const float2 v = __ldg((const float2*)p);
+    return mk(v.x, v.y);
+}
+__device__ __forceinline__ cpx<double> ldg(const cpx<double>* p) {
+    const double2 v = __ldg((const double2*)p);
+    return mk(v.x, v.y);
+}
+// multiply by +i (dir = +1) or -i (dir = -1)
+template <class T> __device__ __forceinline__ cpx<T> rot(cpx<T> a, int dir) {
+    return dir > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
+}
+
+// Spectral symbol: scale * L_hat^lpow * (i kappa_deriv, if deriv >= 0), with
+// L_hat = (1 + alpha |kappa|^2)^s and the Nyquist entry of i kappa zeroed.
+struct SymD {
+    double scale;
+    int lpow;
+    int deriv;
+};
+
+// Per-axis symbol tables on the device (length n0, n1, n2/2+1).
+template <class T> struct SpecTabs {
+    const T* dk[3];   // kappa_a with the Nyquist entry zeroed (derivative symbol / i)
+    const T* ksq[3];  // kappa_a^2
+    T alpha;
+    int s;
+};
+
+template <class T>
+__device__ __forceinline__ cpx<T> sym_apply(const SymD& sy, const SpecTabs<T>& tb, int k0, int k1, int k2, cpx<T> v) {
+    T f = (T)sy.scale;
+    if (sy.lpow != 0) {
+        T base = (T)1 + tb.alpha * (tb.ksq[0][k0] + tb.ksq[1][k1] + tb.ksq[2][k2]);
+        int e = tb.s * (sy.lpow > 0 ? sy.lpow : -sy.lpow);
+        T p = (T)1;
+        for (int q = 0; q < e; ++q) p *= base;
+        f = sy.lpow > 0 ? f * p : f / p;
+    }
+    if (sy.deriv >= 0) {
+        int kk = sy.deriv == 0 ? k0 : (sy.deriv == 1 ? k1 : k2);
+        T d = tb.dk[sy.deriv][kk] * f;
+        return mk(-d * v.y, d * v.x);
+    }
+    return mk(f * v.x, f * v.y);
+}
+
+// One FFT axis: length, radix plan, twiddle table e^{-2 pi i t / n}, t < n.
+struct FFTAxis {
+    int n;
+    int nst;
+    int rad[12];
+    const void* tw;
+};
+
+constexpr int MAXI = 4;   // inputs per job
+constexpr int MAXO = 4;   // outputs per job
+constexpr int MAXB = 4;   // un-transformed bases per job
+constexpr int MAXJOBS = 24;
+
+// One transform job inside a pass.
+//  inverse direction: x = sum_i isym[i].scale * in[i];  out[o] = IFFT(osym[o] . x)
+//  forward direction: out[0] = sum_b bcoef[b] * base[b] + sum_i isym[i] . FFT(in[i])
+struct PassJob {
+    const void* in[MAXI];
+    SymD isym[MAXI];
+    void* out[MAXO];
+    SymD osym[MAXO];
+    const void* base[MAXB];
+    double bcoef[MAXB];
+    int nin, nout, nb, pad_;
+};
+
+template <class T> struct PassParams {
+    FFTAxis ax;
+    int n0, n1, n2, n2h;
+    int TL, P, Ph;     // lines per tile, line pitch, half-spectrum pitch (axis-2 pass)
+    int sign;          // -1 forward, +1 inverse
+    SpecTabs<T> tabs;
+    int njobs;
+    PassJob jobs[MAXJOBS];
+};
+
+}  // namespace lddmm

@@ -1,0 +1,1158 @@
+// Host orchestration of the PDE-EPDiff LDDMM hot path on one GPU.
+//
+// Engine<T> owns one device workspace and runs, on one CUDA stream:
+//   * the spectral "program" planner that turns requests of the form
+//       real_out = F^-1[ symbol . (sum_b c_b X_b) ]            (inverse)
+//       spec_out = sum_b c_b B_b + sum_i symbol_i . F(real_i)  (forward)
+//     into the three FFT passes (axis 0, axis 1, axis 2) with fan-out and
+//     combination inside each pass;
+//   * EPDiff shooting (Heun) with semi-Lagrangian map transport (Sec. 2.2,
+//     Sec. 3 of the paper), storing every stage's v, Dv, m = Lv, Dm;
+//   * the forward Jacobi (tangent) sweep and its exact transpose, the adjoint
+//     Jacobi sweep (Sec. 3: incremental EPDiff and the reduced (incremental)
+//     adjoint Jacobi equations with the Gauss-Newton drops);
+//   * the reduced gradient, the Gauss-Newton Hessian-vector product, PCG with
+//     preconditioner K and the Gauss-Newton-Krylov loop (Sec. 2.3, Sec. 3).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "fft_kernels.cuh"
+#include "lddmm.h"
+#include "pw_kernels.cuh"
+
+namespace lddmm {
+
+struct EngineBase {
+    virtual ~EngineBase() {}
+    virtual lddmm_status shoot(const void* v0, const void* I0, void* m1, void* u1, double* kinetic) = 0;
+    virtual lddmm_status gradient(const void* v0, const void* I0, const void* I1, void* grad, double* energy) = 0;
+    virtual lddmm_status hessvec(const void* dv0, void* Hdv) = 0;
+    virtual lddmm_status jacobi_forward(const void* dv0, void* eta1, void* xi1) = 0;
+    virtual lddmm_status jacobi_adjoint(const void* beta, const void* bxi, void* out) = 0;
+    virtual lddmm_status apply_metric(const void* in, void* out, int ncomp, int power) = 0;
+    virtual lddmm_status jacobian_det(const void* u, void* J, double* minmax) = 0;
+    virtual lddmm_status reg(const void* I0, const void* I1, void* v0, lddmm_report* rep) = 0;
+    virtual lddmm_status synchronize() = 0;
+    lddmm_status status = LDDMM_OK;
+};
+
+// ------------------------------------------------------------------ sizes
+struct Dims {
+    int n0, n1, n2, n2h;
+    size_t N, NS, rows;
+    double len[3], h[3], cell;
+};
+
+inline bool axis_ok(int n) {
+    if (n < 2 || n > 512) return false;
+    int m = n;
+    for (int r : {2, 3, 5})
+        while (m % r == 0) m /= r;
+    return m == 1;
+}
+
+inline bool make_dims(const lddmm_grid* g, Dims* d) {
+    if (!g) return false;
+    for (int a = 0; a < 3; ++a)
+        if (!axis_ok(g->n[a])) return false;
+    d->n0 = g->n[0];
+    d->n1 = g->n[1];
+    d->n2 = g->n[2];
+    d->n2h = d->n2 / 2 + 1;
+    d->N = (size_t)d->n0 * d->n1 * d->n2;
+    d->NS = (size_t)d->n0 * d->n1 * d->n2h;
+    d->rows = (size_t)d->n0 * d->n1;
+    d->cell = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        d->len[a] = g->len[a] > 0 ? g->len[a] : 2.0 * M_PI;
+        d->h[a] = d->len[a] / g->n[a];
+        d->cell *= d->h[a];
+    }
+    return true;
+}
+
+constexpr int POOL = 48;   // partial spectra for the planner
+constexpr int RSCR = 42;   // real scratch fields
+constexpr int NSLOT = 64;  // device double result slots
+
+// Workspace layout (element counts).  Shared by the allocator and by
+// lddmm_workspace_bytes so admission control sees the true footprint.
+struct Layout {
+    size_t spec_fields, real_fields, bytes;
+};
+inline Layout layout_for(const Dims& d, const lddmm_params* p, size_t tsize) {
+    Layout L;
+    // pool + vhat(6) + v0hat(3) + R1(3) + tan(12) + tb(6) + adj(12) + adja(6) + dhat(3) + tmp(3)
+    L.spec_fields = POOL + 6 + 3 + 3 + 12 + 6 + 12 + 6 + 3 + 3;
+    // states + vfin(6) + u(6) + scratch + m1(1) + gm1(3) + r(1) + PCG (x r z p q g vt: 21)
+    L.real_fields = (size_t)2 * p->nt * 24 + 6 + 6 + RSCR + 1 + 3 + 1 + 21;
+    size_t b = L.spec_fields * d.NS * 2 * tsize + L.real_fields * d.N * tsize;
+    b += (size_t)(d.n0 + d.n1 + d.n2) * 2 * tsize * 2;  // twiddles
+    b += (size_t)(d.n0 + d.n1 + d.n2h) * tsize * 2;      // symbol tables
+    b += (RED_BLOCKS * 3 + NSLOT) * sizeof(double);
+    b += 64 * 256;                                       // alignment slack
+    L.bytes = b;
+    return L;
+}
+
+inline std::vector<int> radix_plan(int n) {
+    std::vector<int> r;
+    int m = n;
+    while (m % 4 == 0) {
+        r.push_back(4);
+        m /= 4;
+    }
+    while (m % 2 == 0) {
+        r.push_back(2);
+        m /= 2;
+    }
+    while (m % 3 == 0) {
+        r.push_back(3);
+        m /= 3;
+    }
+    while (m % 5 == 0) {
+        r.push_back(5);
+        m /= 5;
+    }
+    return r;
+}
+
+#define LD_CK(call)                                           \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return fail(LDDMM_ERR_CUDA);   \
+    } while (0)
+
+template <class T>
+class Engine : public EngineBase {
+   public:
+    using C = cpx<T>;
+
+    struct SpecLin {
+        const C* p[MAXI];
+        double c[MAXI];
+        int n;
+    };
+    struct InvReq {
+        int src;
+        SymD sym;
+        T* out;
+    };
+    struct FwdTerm {
+        const T* in;
+        SymD sym;
+    };
+    struct FwdOut {
+        C* out;
+        std::vector<FwdTerm> terms;
+        std::vector<std::pair<const C*, double>> bases;
+    };
+
+    Dims d;
+    lddmm_params prm;
+    cudaStream_t st;
+    unsigned char* base_ = nullptr;
+    size_t off_ = 0, cap_ = 0;
+
+    // device buffers
+    C* pool[POOL];
+    C *vhat[2], *v0hat, *R1, *tan_[2], *tb, *adj[2], *adja, *dhat, *tmp;
+    T *states, *vfin, *ubuf[2], *rs, *m1, *gm1, *rbuf;
+    T *px, *pr, *pz, *pp, *pq, *pg, *pvt;
+    double *partial, *dres, *hres = nullptr;
+    FFTAxis ax[3];
+    SpecTabs<T> tabs;
+    int TLc[2], Pc[2], TL2, P2, Ph2;
+    size_t smem_c[2], smem2;
+    int pool_top = 0;
+    bool lin_valid = false;
+
+    Engine(const Dims& dd, const lddmm_params& p, cudaStream_t s) : d(dd), prm(p), st(s) {}
+
+    ~Engine() override {
+        if (base_) cudaFree(base_);
+        if (hres) cudaFreeHost(hres);
+    }
+
+    lddmm_status fail(lddmm_status s) {
+        if (status == LDDMM_OK) status = s;
+        return status;
+    }
+
+    template <class U>
+    U* carve(size_t count) {
+        size_t o = (off_ + 255) & ~(size_t)255;
+        U* p = (U*)(base_ + o);
+        off_ = o + count * sizeof(U);
+        return p;
+    }
+
+    lddmm_status init() {
+        Layout L = layout_for(d, &prm, sizeof(T));
+        cap_ = L.bytes;
+        if (cudaMalloc(&base_, cap_) != cudaSuccess) {
+            base_ = nullptr;
+            cudaGetLastError();
+            return fail(LDDMM_ERR_OOM);
+        }
+        if (cudaMallocHost(&hres, NSLOT * sizeof(double)) != cudaSuccess) {
+            hres = nullptr;
+            return fail(LDDMM_ERR_OOM);
+        }
+        for (int i = 0; i < POOL; ++i) pool[i] = carve<C>(d.NS);
+        for (int i = 0; i < 2; ++i) vhat[i] = carve<C>(3 * d.NS);
+        v0hat = carve<C>(3 * d.NS);
+        R1 = carve<C>(3 * d.NS);
+        for (int i = 0; i < 2; ++i) tan_[i] = carve<C>(6 * d.NS);
+        tb = carve<C>(6 * d.NS);
+        for (int i = 0; i < 2; ++i) adj[i] = carve<C>(6 * d.NS);
+        adja = carve<C>(6 * d.NS);
+        dhat = carve<C>(3 * d.NS);
+        tmp = carve<C>(3 * d.NS);
+        states = carve<T>((size_t)2 * prm.nt * 24 * d.N);
+        vfin = carve<T>(6 * d.N);
+        for (int i = 0; i < 2; ++i) ubuf[i] = carve<T>(3 * d.N);
+        rs = carve<T>((size_t)RSCR * d.N);
+        m1 = carve<T>(d.N);
+        gm1 = carve<T>(3 * d.N);
+        rbuf = carve<T>(d.N);
+        px = carve<T>(3 * d.N);
+        pr = carve<T>(3 * d.N);
+        pz = carve<T>(3 * d.N);
+        pp = carve<T>(3 * d.N);
+        pq = carve<T>(3 * d.N);
+        pg = carve<T>(3 * d.N);
+        pvt = carve<T>(3 * d.N);
+        partial = carve<double>(RED_BLOCKS * 3);
+        dres = carve<double>(NSLOT);
+        LD_CK(cudaMemset(base_, 0, off_));
+        // twiddles and symbol tables
+        const int ns[3] = {d.n0, d.n1, d.n2};
+        for (int a = 0; a < 3; ++a) {
+            const int n = ns[a];
+            std::vector<int> rp = radix_plan(n);
+            ax[a].n = n;
+            ax[a].nst = (int)rp.size();
+            for (int i = 0; i < (int)rp.size(); ++i) ax[a].rad[i] = rp[i];
+            std::vector<C> tw(n);
+            for (int t = 0; t < n; ++t) {
+                long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)t / (long double)n;
+                tw[t].x = (T)cosl(ang);
+                tw[t].y = (T)sinl(ang);
+            }
+            C* dtw = carve<C>(n);
+            LD_CK(cudaMemcpy(dtw, tw.data(), n * sizeof(C), cudaMemcpyHostToDevice));
+            ax[a].tw = dtw;
+        }
+        const int nk[3] = {d.n0, d.n1, d.n2h};
+        for (int a = 0; a < 3; ++a) {
+            std::vector<T> dk(nk[a]), ks(nk[a]);
+            const int n = ns[a];
+            for (int k = 0; k < nk[a]; ++k) {
+                int sk = (a < 2 && k >= (n + 1) / 2) ? k - n : k;
+                double kap = 2.0 * M_PI / d.len[a] * sk;
+                ks[k] = (T)(kap * kap);
+                bool nyq = (n % 2 == 0) && (k == n / 2);
+                dk[k] = nyq ? (T)0 : (T)kap;
+            }
+            T* ddk = carve<T>(nk[a]);
+            T* dks = carve<T>(nk[a]);
+            LD_CK(cudaMemcpy(ddk, dk.data(), nk[a] * sizeof(T), cudaMemcpyHostToDevice));
+            LD_CK(cudaMemcpy(dks, ks.data(), nk[a] * sizeof(T), cudaMemcpyHostToDevice));
+            tabs.dk[a] = ddk;
+            tabs.ksq[a] = dks;
+        }
+        tabs.alpha = (T)prm.alpha;
+        tabs.s = prm.s;
+        if (off_ > cap_) return fail(LDDMM_ERR_OOM);
+        // tile geometry
+        const size_t budget = 150 * 1024;
+        for (int a = 0; a < 2; ++a) {
+            const int n = ns[a];
+            Pc[a] = (n % 2 == 0) ? n + 1 : n;
+            TLc[a] = 16;
+            while (TLc[a] > 1 && (size_t)3 * TLc[a] * Pc[a] * sizeof(C) > budget) TLc[a] /= 2;
+            smem_c[a] = (size_t)3 * TLc[a] * Pc[a] * sizeof(C);
+        }
+        P2 = (d.n2 % 2 == 0) ? d.n2 + 1 : d.n2;
+        Ph2 = (d.n2h % 2 == 0) ? d.n2h + 1 : d.n2h;
+        TL2 = 16;
+        while (TL2 > 1 && ((size_t)2 * TL2 * Ph2 + 2 * TL2 * P2) * sizeof(C) > budget) TL2 /= 2;
+        smem2 = ((size_t)2 * TL2 * Ph2 + 2 * TL2 * P2) * sizeof(C);
+        LD_CK(cudaFuncSetAttribute(k_pass_c2c<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c[0]));
+        LD_CK(cudaFuncSetAttribute(k_pass_c2c<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c[1]));
+        LD_CK(cudaFuncSetAttribute(k_pass_axis2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+        LD_CK(cudaDeviceSynchronize());
+        return LDDMM_OK;
+    }
+
+    // ------------------------------------------------------------ helpers
+    C* palloc() {
+        if (pool_top >= POOL) {
+            fail(LDDMM_ERR_DEVICE_CHECK);
+            return pool[POOL - 1];
+        }
+        return pool[pool_top++];
+    }
+    int pw_grid(size_t n) const { return (int)std::min<size_t>((n + PW_THREADS - 1) / PW_THREADS, 152 * 16); }
+    T* state(int s) const { return states + (size_t)s * 24 * d.N; }
+    double dt() const { return 1.0 / prm.nt; }
+
+    void launch(int axis, int sign, std::vector<PassJob>& jobs) {
+        for (size_t j0 = 0; j0 < jobs.size(); j0 += MAXJOBS) {
+            const int nj = (int)std::min<size_t>(MAXJOBS, jobs.size() - j0);
+            PassParams<T> pp_;
+            pp_.ax = ax[axis];
+            pp_.n0 = d.n0;
+            pp_.n1 = d.n1;
+            pp_.n2 = d.n2;
+            pp_.n2h = d.n2h;
+            pp_.sign = sign;
+            pp_.tabs = tabs;
+            pp_.njobs = nj;
+            for (int j = 0; j < nj; ++j) pp_.jobs[j] = jobs[j0 + j];
+            if (axis == 2) {
+                pp_.TL = TL2;
+                pp_.P = P2;
+                pp_.Ph = Ph2;
+                const int gx = (int)((d.rows + 2 * TL2 - 1) / (2 * TL2));
+                k_pass_axis2<T><<<dim3(gx, nj), FFT_THREADS, smem2, st>>>(pp_);
+            } else if (axis == 1) {
+                pp_.TL = TLc[1];
+                pp_.P = Pc[1];
+                pp_.Ph = 0;
+                const int gx = (int)(((size_t)d.n2h * d.n0 + TLc[1] - 1) / TLc[1]);
+                k_pass_c2c<T, 1><<<dim3(gx, nj), FFT_THREADS, smem_c[1], st>>>(pp_);
+            } else {
+                pp_.TL = TLc[0];
+                pp_.P = Pc[0];
+                pp_.Ph = 0;
+                const int gx = d.n2h * ((d.n1 + TLc[0] - 1) / TLc[0]);
+                k_pass_c2c<T, 0><<<dim3(gx, nj), FFT_THREADS, smem_c[0], st>>>(pp_);
+            }
+        }
+    }
+
+    static PassJob blank() {
+        PassJob j;
+        memset(&j, 0, sizeof(j));
+        return j;
+    }
+    static SymD sym(double s, int l, int dv) {
+        SymD y;
+        y.scale = s;
+        y.lpow = l;
+        y.deriv = dv;
+        return y;
+    }
+
+    // real_out = F^-1[ sym . lincomb(src) ]
+    void inverse(const std::vector<SpecLin>& srcs, const std::vector<InvReq>& reqs) {
+        pool_top = 0;
+        const double invN = 1.0 / (double)d.N;
+        struct K0 {
+            int src, lpow;
+            double scale;
+            bool d0;
+            C* buf;
+        };
+        struct K1 {
+            int k0;
+            bool d1;
+            C* buf;
+        };
+        std::vector<K0> k0s;
+        std::vector<K1> k1s;
+        std::vector<int> r0(reqs.size()), r1(reqs.size());
+        for (size_t r = 0; r < reqs.size(); ++r) {
+            const InvReq& q = reqs[r];
+            const bool d0 = q.sym.deriv == 0;
+            int f = -1;
+            for (size_t i = 0; i < k0s.size(); ++i)
+                if (k0s[i].src == q.src && k0s[i].lpow == q.sym.lpow && k0s[i].scale == q.sym.scale && k0s[i].d0 == d0)
+                    f = (int)i;
+            if (f < 0) {
+                k0s.push_back({q.src, q.sym.lpow, q.sym.scale, d0, palloc()});
+                f = (int)k0s.size() - 1;
+            }
+            r0[r] = f;
+        }
+        for (size_t r = 0; r < reqs.size(); ++r) {
+            const bool d1 = reqs[r].sym.deriv == 1;
+            int f = -1;
+            for (size_t i = 0; i < k1s.size(); ++i)
+                if (k1s[i].k0 == r0[r] && k1s[i].d1 == d1) f = (int)i;
+            if (f < 0) {
+                k1s.push_back({r0[r], d1, palloc()});
+                f = (int)k1s.size() - 1;
+            }
+            r1[r] = f;
+        }
+        // axis 0
+        std::vector<PassJob> jobs;
+        for (size_t s = 0; s < srcs.size(); ++s) {
+            PassJob j = blank();
+            auto flush = [&]() {
+                if (j.nout) jobs.push_back(j);
+                PassJob b = blank();
+                j = b;
+            };
+            auto setin = [&]() {
+                j.nin = srcs[s].n;
+                for (int b = 0; b < srcs[s].n; ++b) {
+                    j.in[b] = srcs[s].p[b];
+                    j.isym[b] = sym(srcs[s].c[b], 0, -1);
+                }
+            };
+            setin();
+            for (size_t i = 0; i < k0s.size(); ++i) {
+                if (k0s[i].src != (int)s) continue;
+                if (j.nout == MAXO) {
+                    flush();
+                    setin();
+                }
+                j.out[j.nout] = k0s[i].buf;
+                j.osym[j.nout] = sym(k0s[i].scale * invN, k0s[i].lpow, k0s[i].d0 ? 0 : -1);
+                j.nout++;
+            }
+            flush();
+        }
+        launch(0, +1, jobs);
+        // axis 1
+        jobs.clear();
+        for (size_t i0 = 0; i0 < k0s.size(); ++i0) {
+            PassJob j = blank();
+            j.nin = 1;
+            j.in[0] = k0s[i0].buf;
+            j.isym[0] = sym(1.0, 0, -1);
+            for (size_t i = 0; i < k1s.size(); ++i) {
+                if (k1s[i].k0 != (int)i0) continue;
+                j.out[j.nout] = k1s[i].buf;
+                j.osym[j.nout] = sym(1.0, 0, k1s[i].d1 ? 1 : -1);
+                j.nout++;
+            }
+            if (j.nout) jobs.push_back(j);
+        }
+        launch(1, +1, jobs);
+        // axis 2
+        jobs.clear();
+        for (size_t i1 = 0; i1 < k1s.size(); ++i1) {
+            PassJob j = blank();
+            auto setin = [&]() {
+                j.nin = 1;
+                j.in[0] = k1s[i1].buf;
+                j.isym[0] = sym(1.0, 0, -1);
+            };
+            setin();
+            for (size_t r = 0; r < reqs.size(); ++r) {
+                if (r1[r] != (int)i1) continue;
+                if (j.nout == MAXO) {
+                    jobs.push_back(j);
+                    j = blank();
+                    setin();
+                }
+                j.out[j.nout] = reqs[r].out;
+                j.osym[j.nout] = sym(1.0, 0, reqs[r].sym.deriv == 2 ? 2 : -1);
+                j.nout++;
+            }
+            if (j.nout) jobs.push_back(j);
+        }
+        launch(2, +1, jobs);
+    }
+
+    // spec_out = sum bases + sum_i sym_i . F(real_i)
+    void forward(const std::vector<FwdOut>& outs) {
+        pool_top = 0;
+        struct G {
+            int o, lpow;
+            double scale;
+            int cls;
+            C* buf;
+            int nin;
+        };
+        // axis 2
+        std::vector<G> g2;
+        std::vector<PassJob> j2;
+        for (size_t o = 0; o < outs.size(); ++o) {
+            for (const FwdTerm& t : outs[o].terms) {
+                const int cls = t.sym.deriv == 0 ? 0 : (t.sym.deriv == 1 ? 1 : 2);
+                int f = -1;
+                for (size_t i = 0; i < g2.size(); ++i)
+                    if (g2[i].o == (int)o && g2[i].lpow == t.sym.lpow && g2[i].scale == t.sym.scale &&
+                        g2[i].cls == cls && g2[i].nin < MAXI)
+                        f = (int)i;
+                if (f < 0) {
+                    g2.push_back({(int)o, t.sym.lpow, t.sym.scale, cls, palloc(), 0});
+                    PassJob j = blank();
+                    j.nout = 1;
+                    j.out[0] = g2.back().buf;
+                    j2.push_back(j);
+                    f = (int)g2.size() - 1;
+                }
+                PassJob& j = j2[f];
+                j.in[j.nin] = t.in;
+                j.isym[j.nin] = sym(1.0, 0, t.sym.deriv == 2 ? 2 : -1);
+                j.nin++;
+                g2[f].nin++;
+            }
+        }
+        launch(2, -1, j2);
+        // axis 1
+        std::vector<G> g1;
+        std::vector<PassJob> j1;
+        for (const G& a : g2) {
+            const int cls0 = a.cls == 0 ? 0 : 1;
+            int f = -1;
+            for (size_t i = 0; i < g1.size(); ++i)
+                if (g1[i].o == a.o && g1[i].lpow == a.lpow && g1[i].scale == a.scale && g1[i].cls == cls0 &&
+                    g1[i].nin < MAXI)
+                    f = (int)i;
+            if (f < 0) {
+                g1.push_back({a.o, a.lpow, a.scale, cls0, palloc(), 0});
+                PassJob j = blank();
+                j.nout = 1;
+                j.out[0] = g1.back().buf;
+                j1.push_back(j);
+                f = (int)g1.size() - 1;
+            }
+            PassJob& j = j1[f];
+            j.in[j.nin] = a.buf;
+            j.isym[j.nin] = sym(1.0, 0, a.cls == 1 ? 1 : -1);
+            j.nin++;
+            g1[f].nin++;
+        }
+        launch(1, -1, j1);
+        // axis 0
+        std::vector<PassJob> j0;
+        for (size_t o = 0; o < outs.size(); ++o) {
+            PassJob j = blank();
+            j.nout = 1;
+            j.out[0] = outs[o].out;
+            for (const G& a : g1) {
+                if (a.o != (int)o) continue;
+                if (j.nin == MAXI) {
+                    fail(LDDMM_ERR_DEVICE_CHECK);
+                    break;
+                }
+                j.in[j.nin] = a.buf;
+                j.isym[j.nin] = sym(a.scale, a.lpow, a.cls == 0 ? 0 : -1);
+                j.nin++;
+            }
+            for (auto& b : outs[o].bases) {
+                if (j.nb == MAXB) {
+                    fail(LDDMM_ERR_DEVICE_CHECK);
+                    break;
+                }
+                j.base[j.nb] = b.first;
+                j.bcoef[j.nb] = b.second;
+                j.nb++;
+            }
+            j0.push_back(j);
+        }
+        launch(0, -1, j0);
+    }
+
+    // comp c of a vector spectral lincomb
+    SpecLin lin(std::initializer_list<std::pair<const C*, double>> terms, int c) const {
+        SpecLin s;
+        s.n = 0;
+        for (auto& t : terms) {
+            s.p[s.n] = t.first + (size_t)c * d.NS;
+            s.c[s.n] = t.second;
+            s.n++;
+        }
+        return s;
+    }
+
+    // real vector field (3 comps) -> spectral
+    void fwd_vec(const T* in, C* out, double scale = 1.0, int lpow = 0) {
+        std::vector<FwdOut> outs(3);
+        for (int c = 0; c < 3; ++c) {
+            outs[c].out = out + c * d.NS;
+            outs[c].terms.push_back({in + c * d.N, sym(scale, lpow, -1)});
+        }
+        forward(outs);
+    }
+    void inv_vec(const C* in, T* out, int ncomp = 3) {
+        std::vector<SpecLin> srcs;
+        std::vector<InvReq> reqs;
+        for (int c = 0; c < ncomp; ++c) {
+            SpecLin s;
+            s.n = 1;
+            s.p[0] = in + c * d.NS;
+            s.c[0] = 1.0;
+            srcs.push_back(s);
+            reqs.push_back({c, sym(1.0, 0, -1), out + c * d.N});
+        }
+        inverse(srcs, reqs);
+    }
+
+    // v, Dv, m = Lv, Dm of a spectral vector lincomb, into the 24-field layout
+    void eval_fields(std::initializer_list<std::pair<const C*, double>> terms, T* S, bool with_m = true) {
+        std::vector<SpecLin> srcs;
+        std::vector<InvReq> reqs;
+        for (int c = 0; c < 3; ++c) srcs.push_back(lin(terms, c));
+        for (int c = 0; c < 3; ++c) {
+            reqs.push_back({c, sym(1.0, 0, -1), S + c * d.N});
+            for (int j = 0; j < 3; ++j) reqs.push_back({c, sym(1.0, 0, j), S + (3 + 3 * c + j) * d.N});
+            if (with_m) {
+                reqs.push_back({c, sym(1.0, 1, -1), S + (12 + c) * d.N});
+                for (int j = 0; j < 3; ++j) reqs.push_back({c, sym(1.0, 1, j), S + (15 + 3 * c + j) * d.N});
+            }
+        }
+        inverse(srcs, reqs);
+    }
+
+    // ------------------------------------------------------------ reductions
+    void dot_async(const T* a, const T* b, size_t n, int slot, double scale) {
+        k_dot_partial<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, partial);
+        k_finish<<<1, RED_THREADS, 0, st>>>(partial, RED_BLOCKS, 1, 0, 0, scale, dres + slot);
+    }
+    void minmax_async(const T* a, size_t n, int slot) {  // slots: max|a|, max a, min a
+        k_absmax_partial<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, n, partial);
+        for (int q = 0; q < 3; ++q)
+            k_finish<<<1, RED_THREADS, 0, st>>>(partial, RED_BLOCKS, 3, q, q == 2 ? 2 : 1, 1.0, dres + slot + q);
+    }
+    lddmm_status fetch(int first, int count) {
+        LD_CK(cudaMemcpyAsync(hres + first, dres + first, count * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LD_CK(cudaStreamSynchronize(st));
+        return LDDMM_OK;
+    }
+    double dot_now(const T* a, const T* b, size_t n) {
+        dot_async(a, b, n, 63, d.cell);
+        if (fetch(63, 1) != LDDMM_OK) return NAN;
+        return hres[63];
+    }
+    lddmm_status check_launch() {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(LDDMM_ERR_CUDA);
+        return status;
+    }
+
+    // ------------------------------------------------------------ shooting
+    // v0 real -> stores every stage's fields, u1 in ubuf[nt%2], kinetic in dres[0..nt]
+    void shoot_core(const T* v0, bool kinetic) {
+        const double dt_ = dt();
+        const int nt = prm.nt;
+        const GridI gi{d.n0, d.n1, d.n2};
+        const T ih0 = (T)(1.0 / d.h[0]), ih1 = (T)(1.0 / d.h[1]), ih2 = (T)(1.0 / d.h[2]);
+        const int cubic = prm.interp == LDDMM_INTERP_CUBIC;
+        fwd_vec(v0, v0hat);
+        cudaMemsetAsync(ubuf[0], 0, 3 * d.N * sizeof(T), st);
+        T* a = rs;
+        for (int k = 0; k < nt; ++k) {
+            C* cur = k == 0 ? v0hat : vhat[k % 2];
+            C* nxt = vhat[(k + 1) % 2];
+            // stage 1 at v_k
+            T* S1 = state(2 * k);
+            eval_fields({{cur, 1.0}}, S1);
+            if (kinetic) dot_async(S1 + 12 * d.N, S1, 3 * d.N, k, d.cell);
+            if (k >= 1)
+                k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, state(2 * (k - 1)), S1, ubuf[(k - 1) % 2],
+                                                                 ubuf[k % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
+            k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S1, d.N}, a, d.N);
+            {
+                std::vector<FwdOut> outs(3);
+                for (int c = 0; c < 3; ++c) {
+                    outs[c].out = R1 + c * d.NS;
+                    outs[c].terms.push_back({a + c * d.N, sym(-1.0, -1, -1)});
+                }
+                forward(outs);
+            }
+            // stage 2 at v*_k = v_k + dt R1
+            T* S2 = state(2 * k + 1);
+            eval_fields({{cur, 1.0}, {R1, dt_}}, S2);
+            k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S2, d.N}, a, d.N);
+            {
+                std::vector<FwdOut> outs(3);
+                for (int c = 0; c < 3; ++c) {
+                    outs[c].out = nxt + c * d.NS;
+                    outs[c].terms.push_back({a + c * d.N, sym(-0.5 * dt_, -1, -1)});
+                    outs[c].bases.push_back({cur + c * d.NS, 1.0});
+                    outs[c].bases.push_back({R1 + c * d.NS, 0.5 * dt_});
+                }
+                forward(outs);
+            }
+        }
+        // v_nt, m_nt in real space, last map step
+        {
+            std::vector<SpecLin> srcs;
+            std::vector<InvReq> reqs;
+            for (int c = 0; c < 3; ++c) {
+                SpecLin s;
+                s.n = 1;
+                s.p[0] = vhat[nt % 2] + c * d.NS;
+                s.c[0] = 1.0;
+                srcs.push_back(s);
+                reqs.push_back({c, sym(1.0, 0, -1), vfin + c * d.N});
+                reqs.push_back({c, sym(1.0, 1, -1), vfin + (3 + c) * d.N});
+            }
+            inverse(srcs, reqs);
+        }
+        if (kinetic) dot_async(vfin + 3 * d.N, vfin, 3 * d.N, nt, d.cell);
+        k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, state(2 * (nt - 1)), vfin, ubuf[(nt - 1) % 2],
+                                                         ubuf[nt % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
+    }
+    T* u1() const { return ubuf[prm.nt % 2]; }
+
+    void warp_and_grad(const T* I0) {
+        const GridI gi{d.n0, d.n1, d.n2};
+        k_warp<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, I0, u1(), m1, (T)(1.0 / d.h[0]), (T)(1.0 / d.h[1]),
+                                                      (T)(1.0 / d.h[2]), prm.interp == LDDMM_INTERP_CUBIC, d.N);
+        std::vector<FwdOut> outs(1);
+        outs[0].out = tmp;
+        outs[0].terms.push_back({m1, sym(1.0, 0, -1)});
+        forward(outs);
+        std::vector<SpecLin> srcs(1);
+        srcs[0].n = 1;
+        srcs[0].p[0] = tmp;
+        srcs[0].c[0] = 1.0;
+        std::vector<InvReq> reqs;
+        for (int j = 0; j < 3; ++j) reqs.push_back({0, sym(1.0, 0, j), gm1 + j * d.N});
+        inverse(srcs, reqs);
+    }
+
+    // ------------------------------------------------------------ Jacobi sweeps
+    // tangent: from tan_[0] = (eta0, xi0); result in tan_[nt % 2]
+    void tangent_sweep() {
+        const double dt_ = dt();
+        T* E = rs;                  // 24 fields
+        T* X = rs + 24 * d.N;       // 12 fields
+        T* pq_ = rs + 36 * d.N;     // 6 fields
+        for (int k = 0; k < prm.nt; ++k) {
+            C* cur = tan_[k % 2];
+            C* nxt = tan_[(k + 1) % 2];
+            C* ce = cur;
+            C* cx = cur + 3 * d.NS;
+            C* be = tb;
+            C* bx = tb + 3 * d.NS;
+            for (int stg = 0; stg < 2; ++stg) {
+                const T* S = state(2 * k + stg);
+                std::vector<SpecLin> srcs;
+                std::vector<InvReq> reqs;
+                for (int c = 0; c < 3; ++c) {
+                    if (stg == 0) srcs.push_back(lin({{ce, 1.0}}, c));
+                    else srcs.push_back(lin({{ce, 1.0}, {be, dt_}}, c));
+                }
+                for (int c = 0; c < 3; ++c) {
+                    if (stg == 0) srcs.push_back(lin({{cx, 1.0}}, c));
+                    else srcs.push_back(lin({{cx, 1.0}, {bx, dt_}}, c));
+                }
+                for (int c = 0; c < 3; ++c) {
+                    reqs.push_back({c, sym(1.0, 0, -1), E + c * d.N});
+                    for (int j = 0; j < 3; ++j) reqs.push_back({c, sym(1.0, 0, j), E + (3 + 3 * c + j) * d.N});
+                    reqs.push_back({c, sym(1.0, 1, -1), E + (12 + c) * d.N});
+                    for (int j = 0; j < 3; ++j) reqs.push_back({c, sym(1.0, 1, j), E + (15 + 3 * c + j) * d.N});
+                    reqs.push_back({3 + c, sym(1.0, 0, -1), X + c * d.N});
+                    for (int j = 0; j < 3; ++j) reqs.push_back({3 + c, sym(1.0, 0, j), X + (3 + 3 * c + j) * d.N});
+                }
+                inverse(srcs, reqs);
+                k_tangent_pw<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S, d.N}, StatePtr<T>{E, d.N}, X,
+                                                                    pq_, d.N);
+                std::vector<FwdOut> outs(6);
+                for (int c = 0; c < 3; ++c) {
+                    FwdOut& oe = outs[c];
+                    FwdOut& ox = outs[3 + c];
+                    if (stg == 0) {
+                        oe.out = be + c * d.NS;
+                        oe.terms.push_back({pq_ + c * d.N, sym(-1.0, -1, -1)});
+                        ox.out = bx + c * d.NS;
+                        ox.terms.push_back({pq_ + (3 + c) * d.N, sym(1.0, 0, -1)});
+                        ox.bases.push_back({ce + c * d.NS, 1.0});
+                    } else {
+                        oe.out = nxt + c * d.NS;
+                        oe.terms.push_back({pq_ + c * d.N, sym(-0.5 * dt_, -1, -1)});
+                        oe.bases.push_back({ce + c * d.NS, 1.0});
+                        oe.bases.push_back({be + c * d.NS, 0.5 * dt_});
+                        ox.out = nxt + (3 + c) * d.NS;
+                        ox.terms.push_back({pq_ + (3 + c) * d.N, sym(0.5 * dt_, 0, -1)});
+                        ox.bases.push_back({cx + c * d.NS, 1.0});
+                        ox.bases.push_back({bx + c * d.NS, 0.5 * dt_});
+                        ox.bases.push_back({ce + c * d.NS, 0.5 * dt_});
+                        ox.bases.push_back({be + c * d.NS, 0.5 * dt_ * dt_});
+                    }
+                }
+                forward(outs);
+            }
+        }
+    }
+
+    // adjoint: from adj[0] = (ybar_eta, ybar_xi) at t = 1; result in adj[nt % 2]
+    void adjoint_sweep() {
+        const double dt_ = dt();
+        T* Y = rs;              // 6 fields
+        T* G = rs + 6 * d.N;    // 36 fields
+        int cur_i = 0;
+        for (int k = prm.nt - 1; k >= 0; --k) {
+            C* cur = adj[cur_i];
+            C* nxt = adj[1 - cur_i];
+            C* ce = cur;
+            C* cx = cur + 3 * d.NS;
+            C* ae = adja;
+            C* axp = adja + 3 * d.NS;
+            for (int stg = 0; stg < 2; ++stg) {
+                const T* S = state(stg == 0 ? 2 * k + 1 : 2 * k);
+                std::vector<SpecLin> srcs;
+                std::vector<InvReq> reqs;
+                for (int c = 0; c < 3; ++c) {
+                    if (stg == 0) srcs.push_back(lin({{ce, 1.0}}, c));
+                    else srcs.push_back(lin({{ce, 0.5 * dt_}, {ae, 0.5 * dt_ * dt_}}, c));
+                }
+                for (int c = 0; c < 3; ++c) {
+                    if (stg == 0) srcs.push_back(lin({{cx, 1.0}}, c));
+                    else srcs.push_back(lin({{cx, 0.5 * dt_}, {axp, 0.5 * dt_ * dt_}}, c));
+                }
+                for (int c = 0; c < 3; ++c) {
+                    reqs.push_back({c, sym(1.0, -1, -1), Y + c * d.N});
+                    reqs.push_back({3 + c, sym(1.0, 0, -1), Y + (3 + c) * d.N});
+                }
+                inverse(srcs, reqs);
+                k_adjoint_pw<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S, d.N}, Y, G, d.N);
+                std::vector<FwdOut> outs(6);
+                for (int c = 0; c < 3; ++c) {
+                    FwdOut& oe = outs[c];
+                    FwdOut& ox = outs[3 + c];
+                    const T* g1 = G + (size_t)(4 * c) * d.N;
+                    const T* g2 = G + (size_t)(4 * (3 + c)) * d.N;
+                    const T* g3 = G + (size_t)(4 * (6 + c)) * d.N;
+                    oe.terms.push_back({g1, sym(1.0, 0, -1)});
+                    oe.terms.push_back({g2, sym(-1.0, 1, -1)});
+                    ox.terms.push_back({g3, sym(1.0, 0, -1)});
+                    for (int j = 0; j < 3; ++j) {
+                        oe.terms.push_back({g1 + (1 + j) * d.N, sym(1.0, 0, j)});
+                        oe.terms.push_back({g2 + (1 + j) * d.N, sym(-1.0, 1, j)});
+                        ox.terms.push_back({g3 + (1 + j) * d.N, sym(1.0, 0, j)});
+                    }
+                    if (stg == 0) {
+                        oe.out = ae + c * d.NS;
+                        oe.bases.push_back({cx + c * d.NS, 1.0});
+                        ox.out = axp + c * d.NS;
+                    } else {
+                        oe.out = nxt + c * d.NS;
+                        oe.bases.push_back({ce + c * d.NS, 1.0});
+                        oe.bases.push_back({ae + c * d.NS, 0.5 * dt_});
+                        oe.bases.push_back({cx + c * d.NS, 0.5 * dt_});
+                        oe.bases.push_back({axp + c * d.NS, 0.5 * dt_ * dt_});
+                        ox.out = nxt + (3 + c) * d.NS;
+                        ox.bases.push_back({cx + c * d.NS, 1.0});
+                        ox.bases.push_back({axp + c * d.NS, 0.5 * dt_});
+                    }
+                }
+                forward(outs);
+            }
+            cur_i = 1 - cur_i;
+        }
+    }
+    C* adj_result() const { return adj[prm.nt % 2]; }
+
+    // spectral out (3) = a_sym . A + b_sym . B  -> real
+    void spec_to_real2(const C* A, SymD sa, const C* B, SymD sb, T* out) {
+        for (int c = 0; c < 3; ++c) {
+            SpecComb<T> sc;
+            sc.nin = 0;
+            if (A) {
+                sc.in[sc.nin] = A + c * d.NS;
+                sc.sym[sc.nin++] = sa;
+            }
+            if (B) {
+                sc.in[sc.nin] = B + c * d.NS;
+                sc.sym[sc.nin++] = sb;
+            }
+            k_spec_comb<T><<<pw_grid(d.NS), PW_THREADS, 0, st>>>(sc, tabs, d.n0, d.n1, d.n2h, tmp + c * d.NS);
+        }
+        inv_vec(tmp, out);
+    }
+
+    // gradient internals: E into dres[nt+1..nt+3]; gradient real in metric `space`
+    void gradient_core(const T* v0, const T* I0, const T* I1, T* grad, int space) {
+        shoot_core(v0, true);
+        warp_and_grad(I0);
+        k_sub<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, rbuf, d.N);
+        dot_async(rbuf, nullptr, d.N, prm.nt + 2, d.cell);
+        k_final_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, gm1, nullptr, rs, 0, d.N);
+        fwd_vec(rs, adj[0] + 3 * d.NS);
+        cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
+        adjoint_sweep();
+        // g_L2 = 2 w L v0 + T^T b ;  V: K g_L2 = 2 w v0 + K T^T b
+        const double w2 = 2.0 * prm.weight;
+        if (space == LDDMM_SPACE_V)
+            spec_to_real2(v0hat, sym(w2, 0, -1), adj_result(), sym(1.0, -1, -1), grad);
+        else
+            spec_to_real2(v0hat, sym(w2, 1, -1), adj_result(), sym(1.0, 0, -1), grad);
+        lin_valid = true;
+    }
+    void hessvec_core(const T* dv0, T* out, int space) {
+        fwd_vec(dv0, dhat);
+        cudaMemcpyAsync(tan_[0], dhat, 3 * d.NS * sizeof(C), cudaMemcpyDeviceToDevice, st);
+        cudaMemsetAsync(tan_[0] + 3 * d.NS, 0, 3 * d.NS * sizeof(C), st);
+        tangent_sweep();
+        T* xi = rs;
+        inv_vec(tan_[prm.nt % 2] + 3 * d.NS, xi);
+        T* c = rs + 3 * d.N;
+        k_final_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, nullptr, gm1, xi, c, 1, d.N);
+        fwd_vec(c, adj[0] + 3 * d.NS);
+        cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
+        adjoint_sweep();
+        const double w2 = 2.0 * prm.weight;
+        if (space == LDDMM_SPACE_V)
+            spec_to_real2(dhat, sym(w2, 0, -1), adj_result(), sym(1.0, -1, -1), out);
+        else
+            spec_to_real2(dhat, sym(w2, 1, -1), adj_result(), sym(1.0, 0, -1), out);
+    }
+
+    // ------------------------------------------------------------ ABI operations
+    lddmm_status shoot(const void* v0, const void* I0, void* m1o, void* u1o, double* kinetic) override {
+        if (status != LDDMM_OK) return status;
+        if (!v0 || (m1o && !I0)) return fail(LDDMM_ERR_ARG);
+        shoot_core((const T*)v0, kinetic != nullptr);
+        lin_valid = false;
+        if (m1o) {
+            const GridI gi{d.n0, d.n1, d.n2};
+            k_warp<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, (const T*)I0, u1(), (T*)m1o, (T)(1.0 / d.h[0]),
+                                                          (T)(1.0 / d.h[1]), (T)(1.0 / d.h[2]),
+                                                          prm.interp == LDDMM_INTERP_CUBIC, d.N);
+        }
+        if (u1o) cudaMemcpyAsync(u1o, u1(), 3 * d.N * sizeof(T), cudaMemcpyDeviceToDevice, st);
+        if (check_launch() != LDDMM_OK) return status;
+        if (kinetic) {
+            if (fetch(0, prm.nt + 1) != LDDMM_OK) return status;
+            for (int k = 0; k <= prm.nt; ++k) kinetic[k] = hres[k];
+        }
+        return status;
+    }
+
+    lddmm_status gradient(const void* v0, const void* I0, const void* I1, void* grad, double* energy) override {
+        if (status != LDDMM_OK) return status;
+        if (!v0 || !I0 || !I1 || !grad) return fail(LDDMM_ERR_ARG);
+        gradient_core((const T*)v0, (const T*)I0, (const T*)I1, (T*)grad, prm.space);
+        if (check_launch() != LDDMM_OK) return status;
+        if (energy) {
+            if (fetch(0, prm.nt + 3) != LDDMM_OK) return status;
+            const double data = hres[prm.nt + 2], reg = prm.weight * hres[0];
+            energy[0] = data + reg;
+            energy[1] = data;
+            energy[2] = reg;
+            if (!std::isfinite(energy[0])) return fail(LDDMM_ERR_NONFINITE);
+        }
+        return status;
+    }
+
+    lddmm_status hessvec(const void* dv0, void* Hdv) override {
+        if (status != LDDMM_OK) return status;
+        if (!dv0 || !Hdv) return fail(LDDMM_ERR_ARG);
+        if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
+        hessvec_core((const T*)dv0, (T*)Hdv, prm.space);
+        return check_launch();
+    }
+
+    lddmm_status jacobi_forward(const void* dv0, void* eta1, void* xi1) override {
+        if (status != LDDMM_OK) return status;
+        if (!dv0) return fail(LDDMM_ERR_ARG);
+        if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
+        fwd_vec((const T*)dv0, tan_[0]);
+        cudaMemsetAsync(tan_[0] + 3 * d.NS, 0, 3 * d.NS * sizeof(C), st);
+        tangent_sweep();
+        if (eta1) inv_vec(tan_[prm.nt % 2], (T*)eta1);
+        if (xi1) inv_vec(tan_[prm.nt % 2] + 3 * d.NS, (T*)xi1);
+        return check_launch();
+    }
+
+    lddmm_status jacobi_adjoint(const void* beta, const void* bxi, void* out) override {
+        if (status != LDDMM_OK) return status;
+        if (!bxi || !out) return fail(LDDMM_ERR_ARG);
+        if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
+        fwd_vec((const T*)bxi, adj[0] + 3 * d.NS);
+        if (beta) fwd_vec((const T*)beta, adj[0]);
+        else cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
+        adjoint_sweep();
+        inv_vec(adj_result(), (T*)out);
+        return check_launch();
+    }
+
+    lddmm_status apply_metric(const void* in, void* out, int ncomp, int power) override {
+        if (status != LDDMM_OK) return status;
+        if (!in || !out || ncomp < 1 || power < -4 || power > 4) return fail(LDDMM_ERR_ARG);
+        for (int c0 = 0; c0 < ncomp; c0 += 3) {
+            const int nc = std::min(3, ncomp - c0);
+            std::vector<FwdOut> outs(nc);
+            for (int c = 0; c < nc; ++c) {
+                outs[c].out = tmp + c * d.NS;
+                outs[c].terms.push_back({(const T*)in + (size_t)(c0 + c) * d.N, sym(1.0, power, -1)});
+            }
+            forward(outs);
+            inv_vec(tmp, (T*)out + (size_t)c0 * d.N, nc);
+        }
+        return check_launch();
+    }
+
+    void jacdet_into(const T* u, T* J) {
+        fwd_vec(u, tmp);
+        std::vector<SpecLin> srcs;
+        std::vector<InvReq> reqs;
+        for (int c = 0; c < 3; ++c) {
+            SpecLin s;
+            s.n = 1;
+            s.p[0] = tmp + c * d.NS;
+            s.c[0] = 1.0;
+            srcs.push_back(s);
+            for (int j = 0; j < 3; ++j) reqs.push_back({c, sym(1.0, 0, j), rs + (3 * c + j) * d.N});
+        }
+        inverse(srcs, reqs);
+        k_jacdet<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(rs, J, d.N);
+    }
+
+    lddmm_status jacobian_det(const void* u, void* J, double* minmax) override {
+        if (status != LDDMM_OK) return status;
+        if (!u) return fail(LDDMM_ERR_ARG);
+        T* Jd = J ? (T*)J : rs + 9 * d.N;
+        jacdet_into((const T*)u, Jd);
+        if (minmax) {
+            minmax_async(Jd, d.N, 60);
+            if (fetch(60, 3) != LDDMM_OK) return status;
+            minmax[0] = hres[62];
+            minmax[1] = hres[61];
+        }
+        return check_launch();
+    }
+
+    lddmm_status synchronize() override {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return fail(LDDMM_ERR_CUDA);
+        return check_launch();
+    }
+
+    // ------------------------------------------------------------ GN-Krylov
+    double energy_at(const T* v, const T* I0, const T* I1) {
+        shoot_core(v, true);
+        lin_valid = false;
+        const GridI gi{d.n0, d.n1, d.n2};
+        k_warp<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, I0, u1(), m1, (T)(1.0 / d.h[0]), (T)(1.0 / d.h[1]),
+                                                      (T)(1.0 / d.h[2]), prm.interp == LDDMM_INTERP_CUBIC, d.N);
+        k_sub<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, rbuf, d.N);
+        dot_async(rbuf, nullptr, d.N, prm.nt + 2, d.cell);
+        if (fetch(0, prm.nt + 3) != LDDMM_OK) return NAN;
+        return hres[prm.nt + 2] + prm.weight * hres[0];
+    }
+
+    void kapply(const T* in, T* out) {  // out = K in (3 comps)
+        fwd_vec(in, tmp, 1.0, -1);
+        inv_vec(tmp, out);
+    }
+
+    lddmm_status reg(const void* I0v, const void* I1v, void* v0v, lddmm_report* rep) override {
+        if (status != LDDMM_OK) return status;
+        if (!I0v || !I1v || !v0v) return fail(LDDMM_ERR_ARG);
+        const T* I0 = (const T*)I0v;
+        const T* I1 = (const T*)I1v;
+        T* v = (T*)v0v;
+        const size_t n3 = 3 * d.N;
+        const int g = pw_grid(n3);
+        lddmm_report R;
+        memset(&R, 0, sizeof(R));
+        double g0max = 0.0;
+        bool ls_fail = false;
+        const int maxit = std::min(prm.gn_maxit, LDDMM_TRACE_MAX);
+        int it = 0;
+        for (; it < maxit; ++it) {
+            gradient_core(v, I0, I1, pg, LDDMM_SPACE_L2);
+            if (fetch(0, prm.nt + 3) != LDDMM_OK) return status;
+            const double E = hres[prm.nt + 2] + prm.weight * hres[0];
+            if (!std::isfinite(E)) return fail(LDDMM_ERR_NONFINITE);
+            R.energy[it] = E;
+            // |g|_inf in the chosen metric
+            const T* gsp = pg;
+            if (prm.space == LDDMM_SPACE_V) {
+                kapply(pg, pz);
+                gsp = pz;
+            }
+            minmax_async(gsp, n3, 60);
+            if (fetch(60, 1) != LDDMM_OK) return status;
+            if (it == 0) g0max = hres[60];
+            // PCG on H x = -g, preconditioner K, x0 = 0
+            cudaMemsetAsync(px, 0, n3 * sizeof(T), st);
+            k_lincomb2<T><<<g, PW_THREADS, 0, st>>>((T)-1, pg, (T)0, pg, pr, n3);
+            kapply(pr, pz);
+            cudaMemcpyAsync(pp, pz, n3 * sizeof(T), cudaMemcpyDeviceToDevice, st);
+            double rz = dot_now(pr, pz, n3);
+            const double nrm0 = prm.space == LDDMM_SPACE_V ? std::sqrt(std::max(rz, 0.0)) : std::sqrt(dot_now(pr, pr, n3));
+            int pit = 0;
+            while (pit < prm.pcg_maxit) {
+                hessvec_core(pp, pq, LDDMM_SPACE_L2);
+                const double pq_ = dot_now(pp, pq, n3);
+                if (!(pq_ > 0.0)) break;
+                const double alpha = rz / pq_;
+                k_axpby<T><<<g, PW_THREADS, 0, st>>>((T)alpha, pp, (T)1, px, n3);
+                k_axpby<T><<<g, PW_THREADS, 0, st>>>((T)-alpha, pq, (T)1, pr, n3);
+                kapply(pr, pz);
+                const double rzn = dot_now(pr, pz, n3);
+                ++pit;
+                const double res =
+                    prm.space == LDDMM_SPACE_V ? std::sqrt(std::max(rzn, 0.0)) : std::sqrt(dot_now(pr, pr, n3));
+                if (res <= prm.pcg_rtol * nrm0) break;
+                const double beta = rzn / rz;
+                k_axpby<T><<<g, PW_THREADS, 0, st>>>((T)1, pz, (T)beta, pp, n3);
+                rz = rzn;
+            }
+            R.pcg_iters[it] = pit;
+            R.pcg_iters_total += pit;
+            const double slope = dot_now(pg, px, n3);
+            double eps = 1.0;
+            bool ok = false;
+            for (int t = 0; t < prm.ls_maxit; ++t) {
+                k_lincomb2<T><<<g, PW_THREADS, 0, st>>>((T)1, v, (T)eps, px, pvt, n3);
+                const double Et = energy_at(pvt, I0, I1);
+                if (status != LDDMM_OK) return status;
+                if (std::isfinite(Et) && Et <= E + prm.armijo_c1 * eps * slope) {
+                    ok = true;
+                    break;
+                }
+                eps *= 0.5;
+            }
+            R.step[it] = ok ? eps : 0.0;
+            if (!ok) {
+                ls_fail = true;
+                ++it;
+                break;
+            }
+            cudaMemcpyAsync(v, pvt, n3 * sizeof(T), cudaMemcpyDeviceToDevice, st);
+        }
+        R.gn_iters = it;
+        // final metrics: energy, relative gradient, MSE_rel, Jacobian extrema
+        gradient_core(v, I0, I1, pg, LDDMM_SPACE_L2);
+        if (fetch(0, prm.nt + 3) != LDDMM_OK) return status;
+        R.energy[it] = hres[prm.nt + 2] + prm.weight * hres[0];
+        const double data = hres[prm.nt + 2];
+        const T* gsp = pg;
+        if (prm.space == LDDMM_SPACE_V) {
+            kapply(pg, pz);
+            gsp = pz;
+        }
+        minmax_async(gsp, n3, 60);
+        if (fetch(60, 1) != LDDMM_OK) return status;
+        R.gnorm_rel = g0max > 0 ? hres[60] / g0max : 0.0;
+        k_sub<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(I0, I1, rbuf, d.N);
+        const double d0 = dot_now(rbuf, nullptr, d.N);
+        R.mse_rel = d0 > 0 ? data / d0 : 0.0;
+        T* J = rs + 9 * d.N;
+        jacdet_into(u1(), J);
+        minmax_async(J, d.N, 60);
+        if (fetch(60, 3) != LDDMM_OK) return status;
+        R.jac_max = hres[61];
+        R.jac_min = hres[62];
+        if (check_launch() != LDDMM_OK) return status;
+        if (rep) *rep = R;
+        if (!std::isfinite(R.energy[it])) return fail(LDDMM_ERR_NONFINITE);
+        return ls_fail ? LDDMM_WARN_LINESEARCH : LDDMM_OK;
+    }
+};
+
+EngineBase* make_engine_f64(const Dims& d, const lddmm_params& p, cudaStream_t s, lddmm_status* st);
+EngineBase* make_engine_f32(const Dims& d, const lddmm_params& p, cudaStream_t s, lddmm_status* st);
+
+}  // namespace lddmm

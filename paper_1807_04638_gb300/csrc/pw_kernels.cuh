@@ -1,0 +1,381 @@
+// Pointwise kernels on real fields: the ad* / ad bilinear forms of the EPDiff
+// equation and of the Jacobi sweeps, semi-Lagrangian transport, warping,
+// Jacobian determinants and double-precision reductions.
+//
+// A time state holds 24 real fields, each N = n0*n1*n2 values:
+//   [0..2]   v_c          [3 + 3c + j]  D_j v_c
+//   [12..14] m_c = (L v)_c [15 + 3c + j] D_j m_c
+#pragma once
+#include "common.cuh"
+
+namespace lddmm {
+
+constexpr int PW_THREADS = 256;
+
+template <class T> struct StatePtr {
+    const T* p;  // 24 fields, stride N
+    size_t N;
+    __device__ __forceinline__ T v(int c, size_t x) const { return p[c * N + x]; }
+    __device__ __forceinline__ T Dv(int c, int j, size_t x) const { return p[(3 + 3 * c + j) * N + x]; }
+    __device__ __forceinline__ T m(int c, size_t x) const { return p[(12 + c) * N + x]; }
+    __device__ __forceinline__ T Dm(int c, int j, size_t x) const { return p[(15 + 3 * c + j) * N + x]; }
+};
+
+// ad*_v m = (Dv)^T m + (Dm) v + m div v  (EPDiff bracket, Sec. 2.2)
+template <class T>
+__global__ void k_adstar(StatePtr<T> S, T* __restrict__ out, size_t N) {
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        T v[3], m[3], Dv[3][3], Dm[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[c] = S.v(c, x);
+            m[c] = S.m(c, x);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                Dv[c][j] = S.Dv(c, j, x);
+                Dm[c][j] = S.Dm(c, j, x);
+            }
+        }
+        const T divv = Dv[0][0] + Dv[1][1] + Dv[2][2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T a = m[i] * divv;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) a += Dv[j][i] * m[j] + Dm[i][j] * v[j];
+            out[i * N + x] = a;
+        }
+    }
+}
+
+// Tangent (forward Jacobi) stage, pointwise part:
+//  p = ad*_eta m + ad*_v mu  (mu = L eta),   q = ad_v xi = (Dv) xi - (Dxi) v.
+// E holds eta in the 24-field state layout (eta, D eta, mu, D mu);
+// X holds xi (0..2) and D_j xi_c at 3 + 3c + j.
+template <class T>
+__global__ void k_tangent_pw(StatePtr<T> S, StatePtr<T> E, const T* __restrict__ X, T* __restrict__ out, size_t N) {
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        T v[3], m[3], e[3], mu[3], xi[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[c] = S.v(c, x);
+            m[c] = S.m(c, x);
+            e[c] = E.v(c, x);
+            mu[c] = E.m(c, x);
+            xi[c] = X[c * N + x];
+        }
+        const T divv = S.Dv(0, 0, x) + S.Dv(1, 1, x) + S.Dv(2, 2, x);
+        const T dive = E.Dv(0, 0, x) + E.Dv(1, 1, x) + E.Dv(2, 2, x);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T p = m[i] * dive + mu[i] * divv;
+            T q = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                p += E.Dv(j, i, x) * m[j] + S.Dm(i, j, x) * e[j] + S.Dv(j, i, x) * mu[j] + E.Dm(i, j, x) * v[j];
+                q += S.Dv(i, j, x) * xi[j] - X[(3 + 3 * i + j) * N + x] * v[j];
+            }
+            out[i * N + x] = p;
+            out[(3 + i) * N + x] = q;
+        }
+    }
+}
+
+// Adjoint (transposed Jacobi) stage, pointwise part.  Inputs y = K ybar_eta
+// and yx = ybar_xi (3 fields each).  Writes 9 groups of 4 fields
+// [scalar s, f_0, f_1, f_2]; the forward transform of a group is
+// F(s) + sum_j i kappa_j F(f_j):
+//   group c     : R'^T part without L:  s = -sum_i D_c m_i y_i,  f_i = m_c y_i + delta_ic (m.y)
+//   group 3 + c : R'^T part under -L:   s = sum_i D_i v_c y_i + (div v) y_c,  f_j = -v_j y_c
+//   group 6 + c : ad_v^T yx:            s = sum_i D_c v_i yx_i,  f_j = v_j yx_c
+template <class T>
+__global__ void k_adjoint_pw(StatePtr<T> S, const T* __restrict__ Y, T* __restrict__ out, size_t N) {
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        T v[3], m[3], y[3], yx[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[c] = S.v(c, x);
+            m[c] = S.m(c, x);
+            y[c] = Y[c * N + x];
+            yx[c] = Y[(3 + c) * N + x];
+        }
+        const T divv = S.Dv(0, 0, x) + S.Dv(1, 1, x) + S.Dv(2, 2, x);
+        const T my = m[0] * y[0] + m[1] * y[1] + m[2] * y[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T s1 = 0, s2 = divv * y[c], s3 = 0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                s1 -= S.Dm(i, c, x) * y[i];
+                s2 += S.Dv(c, i, x) * y[i];
+                s3 += S.Dv(i, c, x) * yx[i];
+            }
+            T* g1 = out + (size_t)(4 * c) * N;
+            T* g2 = out + (size_t)(4 * (3 + c)) * N;
+            T* g3 = out + (size_t)(4 * (6 + c)) * N;
+            g1[x] = s1;
+            g2[x] = s2;
+            g3[x] = s3;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                g1[(1 + j) * N + x] = m[c] * y[j] + (j == c ? my : (T)0);
+                g2[(1 + j) * N + x] = -v[j] * y[c];
+                g3[(1 + j) * N + x] = v[j] * yx[c];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- interpolation
+struct GridI {
+    int n0, n1, n2;
+};
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+template <class T> __device__ __forceinline__ void cr_weights(T t, T* w) {
+    const T t2 = t * t, t3 = t2 * t;
+    w[0] = (T)0.5 * (-t3 + (T)2 * t2 - t);
+    w[1] = (T)0.5 * ((T)3 * t3 - (T)5 * t2 + (T)2);
+    w[2] = (T)0.5 * ((T)-3 * t3 + (T)4 * t2 + t);
+    w[3] = (T)0.5 * (t3 - t2);
+}
+
+// Interpolate NC fields (stride N) at voxel (i0,i1,i2) + d (d in voxels).
+template <class T, int NC>
+__device__ __forceinline__ void interp_at(const T* __restrict__ f, size_t N, GridI g, int i0, int i1, int i2,
+                                          const T d[3], int cubic, T* res) {
+    int base[3];
+    T w[3][4];
+    const int ii[3] = {i0, i1, i2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T fl = floor(d[a]);
+        const T t = d[a] - fl;
+        base[a] = ii[a] + (int)fl;
+        if (cubic) {
+            cr_weights(t, w[a]);
+        } else {
+            w[a][0] = (T)1 - t;
+            w[a][1] = t;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) res[c] = 0;
+    const int lo = cubic ? -1 : 0, cnt = cubic ? 4 : 2;
+    for (int a0 = 0; a0 < cnt; ++a0) {
+        const size_t o0 = (size_t)wrapi(base[0] + lo + a0, g.n0) * g.n1;
+        for (int a1 = 0; a1 < cnt; ++a1) {
+            const size_t o1 = (o0 + wrapi(base[1] + lo + a1, g.n1)) * g.n2;
+            const T w01 = w[0][a0] * w[1][a1];
+            for (int a2 = 0; a2 < cnt; ++a2) {
+                const size_t o = o1 + wrapi(base[2] + lo + a2, g.n2);
+                const T ww = w01 * w[2][a2];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) res[c] += ww * __ldg(&f[c * N + o]);
+            }
+        }
+    }
+}
+
+// One semi-Lagrangian step of the inverse-map displacement u (psi = x + u):
+//   Xt = x - dt v1(x);  X = x - dt/2 (v1(x) + v0(Xt));  u1(x) = (X - x) + u0(X).
+template <class T>
+__global__ void k_sl_step(GridI g, const T* __restrict__ v0, const T* __restrict__ v1, const T* __restrict__ u0,
+                          T* __restrict__ u1, T dt, T ih0, T ih1, T ih2, int cubic, size_t N) {
+    const T ih[3] = {ih0, ih1, ih2};
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        const int i2 = (int)(x % g.n2);
+        const int i1 = (int)((x / g.n2) % g.n1);
+        const int i0 = (int)(x / ((size_t)g.n2 * g.n1));
+        T w1[3], d[3], vt[3], ut[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            w1[c] = v1[c * N + x];
+            d[c] = -dt * w1[c] * ih[c];
+        }
+        interp_at<T, 3>(v0, N, g, i0, i1, i2, d, cubic, vt);
+        T disp[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            disp[c] = (T)-0.5 * dt * (w1[c] + vt[c]);
+            d[c] = disp[c] * ih[c];
+        }
+        interp_at<T, 3>(u0, N, g, i0, i1, i2, d, cubic, ut);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u1[c * N + x] = disp[c] + ut[c];
+    }
+}
+
+// m(x) = I(x + u(x))
+template <class T>
+__global__ void k_warp(GridI g, const T* __restrict__ img, const T* __restrict__ u, T* __restrict__ out, T ih0, T ih1,
+                       T ih2, int cubic, size_t N) {
+    const T ih[3] = {ih0, ih1, ih2};
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        const int i2 = (int)(x % g.n2);
+        const int i1 = (int)((x / g.n2) % g.n1);
+        const int i0 = (int)(x / ((size_t)g.n2 * g.n1));
+        T d[3], r[1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[c] = u[c * N + x] * ih[c];
+        interp_at<T, 1>(img, N, g, i0, i1, i2, d, cubic, r);
+        out[x] = r[0];
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+// Deterministic two-phase double reductions: block partials, then one block.
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 592;  // 4 x 148..152 SMs; partial buffer size
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// op: 0 sum, 1 max, 2 min
+__device__ __forceinline__ double block_reduce(double v, int op) {
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = op == 0 ? warp_sum(v) : (op == 1 ? warp_max(v) : warp_min(v));
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    const double id = op == 0 ? 0.0 : (op == 1 ? -1.0e300 : 1.0e300);
+    v = threadIdx.x < nw ? sh[threadIdx.x] : id;
+    if (wid == 0) v = op == 0 ? warp_sum(v) : (op == 1 ? warp_max(v) : warp_min(v));
+    __syncthreads();
+    return v;
+}
+
+// partial[b] = sum over this block's share of a[x]*b[x] (b == nullptr: a[x]^2)
+template <class T>
+__global__ void k_dot_partial(const T* __restrict__ a, const T* __restrict__ b, size_t n, double* __restrict__ partial) {
+    double acc = 0.0;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+        const double av = (double)a[x];
+        acc += av * (b ? (double)b[x] : av);
+    }
+    acc = block_reduce(acc, 0);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// partial[3*b + {0,1,2}] = {max|a|, max a, min a}
+template <class T>
+__global__ void k_absmax_partial(const T* __restrict__ a, size_t n, double* __restrict__ partial) {
+    double am = 0.0, mx = -1.0e300, mn = 1.0e300;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+        const double v = (double)a[x];
+        am = fmax(am, fabs(v));
+        mx = fmax(mx, v);
+        mn = fmin(mn, v);
+        if (v != v) am = 1.0e308;  // NaN poisons max|a|
+    }
+    am = block_reduce(am, 1);
+    mx = block_reduce(mx, 1);
+    mn = block_reduce(mn, 2);
+    if (threadIdx.x == 0) {
+        partial[3 * blockIdx.x] = am;
+        partial[3 * blockIdx.x + 1] = mx;
+        partial[3 * blockIdx.x + 2] = mn;
+    }
+}
+
+// out[slot] = scale * reduce(partial[0..nb*stride) with the given stride/offset)
+static __global__ void k_finish(const double* __restrict__ partial, int nb, int stride, int off, int op, double scale,
+                         double* __restrict__ out) {
+    const double id = op == 0 ? 0.0 : (op == 1 ? -1.0e300 : 1.0e300);
+    double v = id;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const double p = partial[i * stride + off];
+        v = op == 0 ? v + p : (op == 1 ? fmax(v, p) : fmin(v, p));
+    }
+    v = block_reduce(v, op);
+    if (threadIdx.x == 0) *out = scale * v;
+}
+
+// ---------------------------------------------------------------- small pointwise ops
+// y = a*x + b*y  over n values
+template <class T>
+__global__ void k_axpby(T a, const T* __restrict__ x, T b, T* __restrict__ y, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+// z = a*x + b*y
+template <class T>
+__global__ void k_lincomb2(T a, const T* __restrict__ x, T b, const T* __restrict__ y, T* __restrict__ z, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        z[i] = a * x[i] + b * y[i];
+}
+
+// Final-time sources.  mode 0 (gradient):  out_c = -2 (m1 - I1) grad_c m1
+//                      mode 1 (Gauss-Newton): out_c = 2 (grad m1 . xi) grad_c m1
+template <class T>
+__global__ void k_final_source(const T* __restrict__ m1, const T* __restrict__ I1, const T* __restrict__ gm,
+                               const T* __restrict__ xi, T* __restrict__ out, int mode, size_t N) {
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        const T g0 = gm[x], g1 = gm[N + x], g2 = gm[2 * N + x];
+        T f;
+        if (mode == 0) f = (T)-2 * (m1[x] - I1[x]);
+        else f = (T)2 * (g0 * xi[x] + g1 * xi[N + x] + g2 * xi[2 * N + x]);
+        out[x] = f * g0;
+        out[N + x] = f * g1;
+        out[2 * N + x] = f * g2;
+    }
+}
+
+// r = m1 - I1
+template <class T>
+__global__ void k_sub(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ r, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        r[i] = a[i] - b[i];
+}
+
+// det(I + Du), Du[c][j] = D_j u_c at field 3c + j
+template <class T>
+__global__ void k_jacdet(const T* __restrict__ Du, T* __restrict__ J, size_t N) {
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        T a[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) a[c][j] = Du[(3 * c + j) * N + x] + (c == j ? (T)1 : (T)0);
+        J[x] = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+               a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+    }
+}
+
+// Spectral-space combination on [k2][k0][k1] arrays: out = sum_b sym_b . in_b
+template <class T> struct SpecComb {
+    const cpx<T>* in[MAXI];
+    SymD sym[MAXI];
+    int nin;
+};
+template <class T>
+__global__ void k_spec_comb(SpecComb<T> sc, SpecTabs<T> tb, int n0, int n1, int n2h, cpx<T>* __restrict__ out) {
+    const size_t NS = (size_t)n0 * n1 * n2h;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < NS; x += (size_t)gridDim.x * blockDim.x) {
+        const int k1 = (int)(x % n1);
+        const int k0 = (int)((x / n1) % n0);
+        const int k2 = (int)(x / ((size_t)n1 * n0));
+        cpx<T> acc = mk((T)0, (T)0);
+        for (int b = 0; b < sc.nin; ++b) acc = acc + sym_apply(sc.sym[b], tb, k0, k1, k2, sc.in[b][x]);
+        out[x] = acc;
+    }
+}
+
+}  // namespace lddmm

@@ -1,0 +1,58 @@
+"""The C-ABI library loads without a GPU and exports every symbol the header
+declares; host-side argument checks work without touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lddmm.h")
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1807_04638_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    return build.LIB
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lddmm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("lddmm_shoot", "lddmm_gradient", "lddmm_hessvec", "lddmm_register"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_side_checks_without_gpu(libpath):
+    import paper_1807_04638_gb300 as pkg
+    p = pkg.default_params()
+    assert p.nt == 10 and p.s == 2 and abs(p.alpha - 0.01) < 1e-15
+    b = pkg.workspace_bytes((32, 32, 32), p)
+    assert b > 2 * 10 * 24 * 32 ** 3 * 8  # at least the stored time states
+    p32 = pkg.default_params(compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32)
+    assert 0 < pkg.workspace_bytes((32, 32, 32), p32) < b
+    # unsupported shapes and bad parameters are rejected before any device work
+    assert pkg.workspace_bytes((7, 32, 32), p) == 0
+    assert pkg.workspace_bytes((32, 32, 1024), p) == 0
+    bad = pkg.default_params(nt=0)
+    assert pkg.workspace_bytes((32, 32, 32), bad) == 0
+    lib = pkg.lib()
+    h = ctypes.c_void_p()
+    g = pkg.make_grid((7, 8, 8))
+    assert lib.lddmm_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(p), None) == 2  # SHAPE
+    assert lib.lddmm_create(None, ctypes.byref(g), ctypes.byref(p), None) == 1  # ARG
+    assert lib.lddmm_shoot(None, None, None, None, None, None) == 1
+    assert lib.lddmm_status_string(5).decode().startswith("no linearisation")

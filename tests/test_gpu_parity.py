@@ -1,0 +1,199 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI, element by element.
+
+Tolerances (relative L2 over the whole array, computed in FP64):
+  FP64 engine: 1e-10 on every array output.
+  FP32 engine: 1e-5 on gradients and Hessian products, 1e-4 on m(1) - I1 and
+  on det(I + D u1).
+Grids span several FFT tiles with ragged tails, radices 2, 3, 5 and an odd
+last axis.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lddmm_oracle as O
+from paper_1807_04638_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-10
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1807_04638_gb300 as p
+    p.lib()
+    return p
+
+
+def dev(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+DT = {"f64": (torch.float64, 0), "f32": (torch.float32, 1)}
+
+
+def params(pkg, prec, **kw):
+    _, cd = DT[prec]
+    return pkg.default_params(compute_dtype=cd, state_dtype=cd, **kw)
+
+
+def problem(n, seed, nt, disp=1.0, kmax=2):
+    g = O.Grid(n, alpha=0.01)
+    I0, vtrue = synth.blob_pair_inputs(n, seed, kmax=kmax, max_disp_vox=disp)
+    I0 = synth.spectral_gaussian_smooth(I0, 1.0)
+    I1 = O.shoot(g, vtrue, nt, I0).m1
+    return g, I0, I1, vtrue
+
+
+GRIDS = [(20, 12, 18), (12, 10, 15), (32, 32, 32)]
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n", [(20, 12, 18), (12, 10, 15), (6, 4, 8)])
+def test_apply_metric(pkg, prec, n):
+    dtype, _ = DT[prec]
+    g = O.Grid(n, alpha=0.03, lengths=(1.0, 2.0, 3.0))
+    f = synth.rng_for(1).standard_normal((3,) + n)
+    tol = F64_TOL if prec == "f64" else 1e-5
+    with pkg.Handle(n, params(pkg, prec, alpha=0.03), lengths=(1.0, 2.0, 3.0)) as h:
+        x = dev(f, dtype)
+        out = torch.empty_like(x)
+        for power, ref in ((-1, g.K(f)), (1, g.L(f)), (0, f)):
+            h.lddmm_apply_metric(x, out, power)
+            h.lddmm_synchronize()
+            assert rel(host(out), ref) < tol, (power, rel(host(out), ref))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n", GRIDS)
+def test_shoot(pkg, prec, n):
+    dtype, _ = DT[prec]
+    nt = 6
+    g, I0, I1, vtrue = problem(n, 3, nt)
+    tr = O.shoot(g, vtrue, nt, I0)
+    with pkg.Handle(n, params(pkg, prec, nt=nt)) as h:
+        m1 = h.new_img()
+        u1 = h.new_vec()
+        kin = h.lddmm_shoot(dev(vtrue, dtype), dev(I0, dtype), m1, u1, kinetic=True)
+    tol_u = F64_TOL if prec == "f64" else 1e-5
+    tol_m = F64_TOL if prec == "f64" else 1e-4
+    assert rel(host(u1), tr.u) < tol_u
+    assert rel(host(m1) - I1, tr.m1 - I1) < tol_m or rel(host(m1), tr.m1) < F64_TOL
+    assert np.allclose(kin, tr.kinetic, rtol=F64_TOL if prec == "f64" else 1e-5, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("space", ["V", "L2"])
+@pytest.mark.parametrize("n", GRIDS)
+def test_gradient_and_hessvec(pkg, prec, space, n):
+    dtype, _ = DT[prec]
+    nt = 5
+    g, I0, I1, vtrue = problem(n, 4, nt)
+    p = O.Params(nt=nt, space=space)
+    v0 = 0.5 * vtrue
+    gl2, E, data, reg, tr = O.gradient(g, p, v0, I0, I1)
+    d = synth.band_limited_field(n, synth.rng_for(7), 3.0, 3) * g.h[0]
+    hl2 = O.hessvec(g, p, tr, d)
+    sp = pkg.LDDMM_SPACE_V if space == "V" else pkg.LDDMM_SPACE_L2
+    tol = F64_TOL if prec == "f64" else 1e-5
+    with pkg.Handle(n, params(pkg, prec, nt=nt, space=sp)) as h:
+        grad = h.new_vec()
+        e = h.lddmm_gradient(dev(v0, dtype), dev(I0, dtype), dev(I1, dtype), grad)
+        hv = h.new_vec()
+        h.lddmm_hessvec(dev(d, dtype), hv)
+        h.lddmm_synchronize()
+    assert abs(e[0] - E) < tol * abs(E) and abs(e[1] - data) < tol * abs(data) and abs(e[2] - reg) < tol * abs(reg)
+    assert rel(host(grad), O.to_space(g, p, gl2)) < tol
+    assert rel(host(hv), O.to_space(g, p, hl2)) < tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_jacobi_sweeps_and_dot_test(pkg, prec):
+    dtype, _ = DT[prec]
+    n = (20, 12, 18)
+    nt = 4
+    g, I0, I1, vtrue = problem(n, 5, nt)
+    p = O.Params(nt=nt)
+    v0 = 0.7 * vtrue
+    tr = O.gradient(g, p, v0, I0, I1)[4]
+    r = synth.rng_for(9)
+    d, be, bx = (r.standard_normal((3,) + n) for _ in range(3))
+    eta, xi = O.tangent(g, tr, d)
+    adj = O.adjoint(g, tr, bx, be)
+    tol = F64_TOL if prec == "f64" else 1e-5
+    with pkg.Handle(n, params(pkg, prec, nt=nt)) as h:
+        grad = h.new_vec()
+        h.lddmm_gradient(dev(v0, dtype), dev(I0, dtype), dev(I1, dtype), grad, energy=False)
+        e1, x1, a0 = h.new_vec(), h.new_vec(), h.new_vec()
+        h.lddmm_jacobi_forward(dev(d, dtype), e1, x1)
+        h.lddmm_jacobi_adjoint(dev(be, dtype), dev(bx, dtype), a0)
+        h.lddmm_synchronize()
+    assert rel(host(e1), eta) < tol and rel(host(x1), xi) < tol
+    assert rel(host(a0), adj) < tol
+    # the GPU sweeps are exact transposes of each other
+    lhs = np.sum(host(e1) * be) + np.sum(host(x1) * bx)
+    rhs = np.sum(d * host(a0))
+    assert abs(lhs - rhs) < (1e-12 if prec == "f64" else 1e-5) * (abs(lhs) + abs(rhs))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_jacobian_det(pkg, prec):
+    dtype, _ = DT[prec]
+    n = (20, 12, 18)
+    g = O.Grid(n)
+    u = synth.band_limited_field(n, synth.rng_for(11), 3.0, 3) * 0.3 * g.h[0]
+    J = O.jacobian_det(g, u)
+    with pkg.Handle(n, params(pkg, prec)) as h:
+        Jd = h.new_img()
+        mm = h.lddmm_jacobian_det(dev(u, dtype), Jd)
+    tol = F64_TOL if prec == "f64" else 1e-4
+    assert rel(host(Jd) - 1.0, J - 1.0) < tol
+    assert abs(mm[0] - J.min()) < tol and abs(mm[1] - J.max()) < tol
+
+
+@pytest.mark.parametrize("interp", ["cubic", "linear"])
+def test_register_replays_oracle(pkg, interp):
+    """Whole registration: the FP64 GPU run and the oracle make the same
+    decisions (PCG iterations, Armijo steps) and reach the same v0."""
+    n = (16, 12, 10)
+    nt = 4
+    g, I0, I1, vtrue = problem(n, 12, nt)
+    p = O.Params(nt=nt, interp=interp)
+    kind = pkg.LDDMM_INTERP_CUBIC if interp == "cubic" else pkg.LDDMM_INTERP_LINEAR
+    with pkg.Handle(n, params(pkg, "f64", nt=nt, interp=kind, gn_maxit=3, pcg_maxit=6)) as h:
+        v = torch.zeros((3,) + n, dtype=torch.float64, device="cuda")
+        rep = h.lddmm_register(dev(I0, torch.float64), dev(I1, torch.float64), v)
+    ref = O.register(g, p, I0, I1, gn_maxit=3, pcg_maxit=6)
+    assert rep["pcg_iters"] == ref.pcg_iters and rep["step"] == ref.steps
+    assert rel(host(v), ref.v0) < 1e-9
+    assert np.allclose(rep["energy"], ref.energies, rtol=1e-9)
+    assert abs(rep["mse_rel"] - ref.mse_rel) < 1e-9 and abs(rep["jac_min"] - ref.jac_min) < 1e-9
+
+
+def test_errors_are_reported(pkg):
+    n = (8, 8, 8)
+    with pytest.raises(pkg.LddmmError):
+        pkg.Handle((7, 8, 8), pkg.default_params())
+    with pkg.Handle(n, pkg.default_params()) as h:
+        out = h.new_vec()
+        with pytest.raises(pkg.LddmmError) as ei:
+            h.lddmm_hessvec(torch.zeros((3,) + n, dtype=torch.float64, device="cuda"), out)
+        assert ei.value.status == 5
+        with pytest.raises(TypeError):
+            h.lddmm_shoot(torch.zeros((3,) + n, dtype=torch.float32, device="cuda"))
