@@ -60,9 +60,14 @@ class Grid:
     first-derivative symbol ``i kappa_a`` has its Nyquist entry zeroed (so the
     discrete derivative is real and exactly skew-symmetric); ``|kappa|^2``
     keeps the Nyquist entry.  ``L_hat = (1 + alpha |kappa|^2)^s``.
+
+    ``dealias``: the spectral projector P keeps the modes with
+    |k_a| <= floor((n_a - 1) / 3) on every axis (the 2/3 rule), so that a
+    product of two band-limited fields is resolved exactly after P.  With
+    ``dealias=False`` P is the identity.
     """
 
-    def __init__(self, n, alpha=0.01, s=2, lengths=None):
+    def __init__(self, n, alpha=0.01, s=2, lengths=None, dealias=True):
         self.n = tuple(int(x) for x in n)
         self.lengths = tuple(float(x) for x in lengths) if lengths is not None else (2 * math.pi,) * 3
         self.h = tuple(l / m for l, m in zip(self.lengths, self.n))
@@ -85,6 +90,12 @@ class Grid:
         self.ksq = ksq
         self.Lhat = (1.0 + self.alpha * ksq) ** self.s
         self.Khat = 1.0 / self.Lhat
+        self.dealias = bool(dealias)
+        cut = [(m - 1) // 3 for m in self.n]
+        inb = [np.abs(k[a]) <= cut[a] for a in range(3)]
+        self.band = (inb[0].reshape(shp[0]) & inb[1].reshape(shp[1]) & inb[2].reshape(shp[2]))
+        if not self.dealias:
+            self.band = np.ones_like(self.band)
         self.coords = np.stack(np.meshgrid(*[np.arange(m, dtype=np.float64) for m in self.n],
                                            indexing="ij"))
 
@@ -118,6 +129,10 @@ class Grid:
 
     def K(self, v):
         return self.inv(self.Khat * self.fwd(v))
+
+    def P(self, v):
+        """2/3-rule projector (identity when dealiasing is off)."""
+        return self.inv(self.band * self.fwd(v)) if self.dealias else np.array(v, dtype=np.float64)
 
     def dot(self, f, g):
         return float(self.cell * np.sum(np.asarray(f) * np.asarray(g)))
@@ -204,20 +219,20 @@ def ad_T(g: Grid, v, y):
 # ---------------------------------------------------------------------------
 
 def epdiff_rhs(g: Grid, v):
-    """R(v) = -K ad*_v (L v)."""
-    return -g.K(ad_star(g, v, g.L(v)))
+    """R(v) = -K P ad*_v (L v)  (P: the dealiasing projector of the products)."""
+    return -g.K(g.P(ad_star(g, v, g.L(v))))
 
 
 def epdiff_rhs_lin(g: Grid, v, eta):
-    """R'(v) eta = -K [ad*_eta (L v) + ad*_v (L eta)]  (incremental EPDiff:
+    """R'(v) eta = -K P [ad*_eta (L v) + ad*_v (L eta)]  (incremental EPDiff:
     d/dt dv = -(ad^dagger_dv v + ad^dagger_v dv))."""
-    return -g.K(ad_star(g, eta, g.L(v)) + ad_star(g, v, g.L(eta)))
+    return -g.K(g.P(ad_star(g, eta, g.L(v)) + ad_star(g, v, g.L(eta))))
 
 
 def epdiff_rhs_lin_T(g: Grid, v, y):
     """Exact grid transpose of eta -> R'(v) eta."""
-    Ky = g.K(y)
-    return -(ad_star_T_first(g, g.L(v), Ky) + g.L(ad_star_T_second(g, v, Ky)))
+    PKy = g.P(g.K(y))
+    return -(ad_star_T_first(g, g.L(v), PKy) + g.L(ad_star_T_second(g, v, PKy)))
 
 
 # ---------------------------------------------------------------------------
@@ -301,10 +316,11 @@ class Trajectory:
 
 
 def shoot(g: Grid, v0, nt, I0=None, kind="cubic"):
-    """Forward geodesic shooting of v0 by Heun steps of the EPDiff equation,
-    with SL transport of the inverse map and the final warp m(1) = I0(x+u)."""
+    """Forward geodesic shooting of P v0 by Heun steps of the EPDiff
+    equation, with SL transport of the inverse map and the final warp
+    m(1) = I0(x+u)."""
     dt = 1.0 / nt
-    v = [np.array(v0, dtype=np.float64)]
+    v = [g.P(v0)]
     vstar = []
     u = np.zeros_like(v[0])
     for k in range(nt):
@@ -329,21 +345,21 @@ def shoot(g: Grid, v0, nt, I0=None, kind="cubic"):
 # ---------------------------------------------------------------------------
 
 def jacobi_A(g: Grid, v, eta, xi):
-    """A_v(eta, xi) = (R'(v) eta, eta + ad_v xi); the Jacobi field equation
+    """A_v(eta, xi) = (R'(v) eta, eta + P ad_v xi); the Jacobi field equation
     xi' = eta + ad_v xi is the right-trivialised variation of the flow."""
-    return epdiff_rhs_lin(g, v, eta), eta + ad(g, v, xi)
+    return epdiff_rhs_lin(g, v, eta), eta + g.P(ad(g, v, xi))
 
 
 def jacobi_A_T(g: Grid, v, yeta, yxi):
     """Exact grid transpose of jacobi_A."""
-    return epdiff_rhs_lin_T(g, v, yeta) + yxi, ad_T(g, v, yxi)
+    return epdiff_rhs_lin_T(g, v, yeta) + yxi, ad_T(g, v, g.P(yxi))
 
 
 def tangent(g: Grid, tr: Trajectory, delta):
     """T: delta v0 -> (eta_nt, xi_nt), Heun on the augmented system reusing the
-    stored states (v_k for stage 1, v*_k for stage 2)."""
+    stored states (v_k for stage 1, v*_k for stage 2), from (P delta, 0)."""
     dt = 1.0 / tr.nt
-    eta = np.array(delta, dtype=np.float64)
+    eta = g.P(delta)
     xi = np.zeros_like(eta)
     for k in range(tr.nt):
         be, bx = jacobi_A(g, tr.v[k], eta, xi)
@@ -370,7 +386,7 @@ def adjoint(g: Grid, tr: Trajectory, b_xi, b_eta=None):
                             0.5 * dt * yx + 0.5 * dt * dt * ax)
         ye = ye + 0.5 * dt * ae + te
         yx = yx + 0.5 * dt * ax + tx
-    return ye
+    return g.P(ye)
 
 
 # ---------------------------------------------------------------------------
@@ -388,12 +404,13 @@ class Params:
 
 
 def energy(g: Grid, p: Params, v0, I0, I1, tr=None):
-    """E(v0) = w <L v0, v0> + ||m(1) - I1||^2; returns (E, data, reg, tr)."""
+    """E(v0) = w <L v0, v0> + ||m(1) - I1||^2 with m(1) shot from P v0;
+    returns (E, data, reg, tr)."""
     if tr is None:
         tr = shoot(g, v0, p.nt, I0, p.interp)
     r = tr.m1 - I1
     data = g.dot(r, r)
-    reg = p.weight * tr.kinetic[0]
+    reg = p.weight * g.dot(g.L(v0), v0)
     return data + reg, data, reg, tr
 
 
