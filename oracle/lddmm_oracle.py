@@ -74,9 +74,10 @@ class Grid:
         self.alpha = float(alpha)
         self.s = int(s)
         self.cell = self.h[0] * self.h[1] * self.h[2]
-        k = [np.fft.fftfreq(self.n[0]) * self.n[0],
-             np.fft.fftfreq(self.n[1]) * self.n[1],
-             np.fft.rfftfreq(self.n[2]) * self.n[2]]
+        # integer wave numbers in FFT order (rounded: fftfreq * n is not exact)
+        k = [np.rint(np.fft.fftfreq(self.n[0]) * self.n[0]),
+             np.rint(np.fft.fftfreq(self.n[1]) * self.n[1]),
+             np.rint(np.fft.rfftfreq(self.n[2]) * self.n[2])]
         kap = [2 * math.pi / self.lengths[a] * k[a] for a in range(3)]
         dsym = []
         for a in range(3):

@@ -444,3 +444,14 @@ def test_gauss_newton_decreases_energy_and_replays():
     again = O.register(g, p, I0, I1, gn_maxit=3, pcg_maxit=5,
                        replay=list(zip(rep.pcg_iters, rep.steps)))
     assert rel(again.v0, rep.v0) < 1e-14
+
+
+@pytest.mark.parametrize("n", [(20, 12, 18), (12, 10, 15), (128, 128, 128), (256, 300, 256)])
+def test_dealias_band_count_closed_form(n):
+    """P keeps exactly (2K0+1)(2K1+1)(K2+1) half-spectrum modes, K_a = (n_a-1)//3,
+    and a product of two band modes never aliases back into the band."""
+    g = O.Grid(n)
+    K = [(m - 1) // 3 for m in n]
+    assert int(g.band.sum()) == (2 * K[0] + 1) * (2 * K[1] + 1) * (K[2] + 1)
+    for a in range(3):
+        assert 2 * K[a] - n[a] < -K[a]  # the alias of the largest sum lies outside the band
