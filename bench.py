@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the PDE-EPDiff LDDMM hot path on GB300.
+
+Headline: Gauss-Newton Hessian-vector products per second at 128^3 (the
+128^3 nested-ellipsoid registration workload: nt = 10, K = (Id - 0.005 Lap)^-2,
+FP32 transport / shooting / K-apply, FP64 reductions).  One step is one Hv:
+forward Jacobi sweep over the stored time states, Gauss-Newton source,
+adjoint Jacobi sweep and assembly, through the C ABI, inputs resident in HBM.
+The line also reports the same metric end to end with host buffers, the
+plain FP64 method, one full registration of the workload, the roofline of
+the dominant kernel class, and the FP64 CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (the path does
+not shard) and value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GN Hessian-vector products/s at 128^3"
+UNIT = "Hv/s"
+N128 = (128, 128, 128)
+NT = 10
+ALPHA = 0.005
+WORKLOAD = ("128^3 registration workload: 3 nested random ellipsoids (0.2/0.5/0.9) + noise 0.02, "
+            "target warped by a random |k|<=6 v0 (6 voxels), nt=10, K=(Id-0.005 Lap)^-2, weight 1e-3, "
+            "Catmull-Rom SL transport, V metric, FP32 form with FP64 reductions")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--registrations", type=int, default=1, help="full registrations to time (0: skip)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- inputs
+def workload_inputs(n=N128, seed=1):
+    """Phantom, true velocity and noise for the 128^3 workload (seeded)."""
+    from paper_1807_04638_gb300 import synth
+    P, v0, e0, e1 = synth.ellipsoid_pair_inputs(n, seed, kmax=6, max_disp_vox=6.0, noise_sigma=0.02)
+    d = synth.band_limited_field(n, synth.rng_for(seed + 1000), 6.0, 3) * (2 * 3.141592653589793 / n[0])
+    return P, v0, e0, e1, d
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_hv_sample(P, v0, d, stages=2):
+    """Time the FP64 oracle on a bounded sample of one Hv at 128^3: `stages`
+    forward Jacobi stages and as many adjoint stages at a fixed linearisation
+    state; scaled by 2 nt / stages to one Hv (a Hv is 2 nt of each)."""
+    import numpy as np
+    from oracle import lddmm_oracle as O
+    g = O.Grid(N128, alpha=ALPHA)
+    v = 0.5 * v0
+    xi = 0.1 * d
+    t0 = time.perf_counter()
+    for _ in range(stages):
+        be, bx = O.jacobi_A(g, v, d, xi)
+        O.jacobi_A_T(g, v, be, bx)
+    dt = time.perf_counter() - t0
+    sec_per_hv = dt * (2 * NT) / stages
+    return 1.0 / sec_per_hv, dt
+
+
+def cpu_cores_used():
+    return 1  # numpy's pocketfft and the elementwise work run on one thread
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    P, v0, e0, e1, d = workload_inputs()
+    for _ in range(args.warmup):
+        oracle_hv_sample(P, v0, d, stages=1)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, _ = oracle_hv_sample(P, v0, d, stages=1)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = args.steps / sum(1.0 / v for v in vals)
+    sample = ("per step: one forward Jacobi stage + one adjoint Jacobi stage of the FP64 NumPy oracle at 128^3 "
+              "(fixed linearisation state), scaled by 2*nt = 20 to one Hv")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": list(N128), "nt": NT},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- native arm
+def run_native(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_1807_04638_gb300 as pkg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+
+    def barrier():
+        if dist:
+            td.barrier()
+
+    P, v0t, e0, e1, d = workload_inputs()
+    f32 = torch.float32
+    T = lambda a, dt=f32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    prm = pkg.default_params(alpha=ALPHA, nt=NT, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32,
+                             gn_maxit=10, pcg_maxit=50, pcg_rtol=0.1)
+    stream = torch.cuda.current_stream(dev)
+    h = pkg.Handle(N128, prm, stream=stream, device=dev.index)
+    # target: phantom warped by the true velocity (library shoot), plus noise
+    I0 = T(P + e0)
+    m1 = h.new_img()
+    h.lddmm_shoot(T(v0t), T(P), m1)
+    I1 = (m1 + T(e1)).contiguous()
+    v0 = T(0.5 * v0t)
+    grad = h.new_vec()
+    h.lddmm_gradient(v0, I0, I1, grad, energy=True)
+    delta = T(d)
+    hv = h.new_vec()
+
+    # ---- device-resident timing
+    for _ in range(args.warmup):
+        h.lddmm_hessvec(delta, hv)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clk = ClockSampler(dev.index)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        h.lddmm_hessvec(delta, hv)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1000.0)
+    hv_host = hv.double().cpu().numpy()
+    finite = bool(np.isfinite(hv_host).all())
+
+    # ---- end to end through the public API with pinned host buffers
+    hd = torch.tensor(np.ascontiguousarray(d), dtype=f32).pin_memory()
+    ho = torch.empty_like(hd).pin_memory()
+    dbuf = h.new_vec()
+    for _ in range(2):
+        dbuf.copy_(hd, non_blocking=True)
+        h.lddmm_hessvec(dbuf, hv)
+        ho.copy_(hv, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ee0.record(stream)
+    for _ in range(args.steps):
+        dbuf.copy_(hd, non_blocking=True)
+        h.lddmm_hessvec(dbuf, hv)
+        ho.copy_(hv, non_blocking=True)
+    ee1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ems = ee0.elapsed_time(ee1)
+    if dist:
+        t = torch.tensor([ems], device=dev)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ems = float(t.item())
+    e2e_value = world * args.steps / (ems / 1000.0)
+    vec_bytes = 3 * int(np.prod(N128)) * 4
+
+    # ---- kernel classes: CUDA events around every launch (separate pass)
+    h.lddmm_profile(True)
+    nprof = 3
+    for _ in range(nprof):
+        h.lddmm_hessvec(delta, hv)
+    prof = h.lddmm_profile_read()
+    h.lddmm_profile(False)
+    tot_ms = sum(v[0] for v in prof.values())
+    launches_per_hv = sum(v[2] for v in prof.values()) / nprof
+    dom = max(prof, key=lambda k: prof[k][0])
+    dms, dbytes, dn = prof[dom]
+    peak, peak_kind = load_peaks()
+    achieved = (dbytes / dn) / ((dms / dn) / 1000.0) / 1e9 if dn else None
+    shares = {k: {"share": round(v[0] / tot_ms, 4), "launches_per_hv": v[2] / nprof,
+                  "gbs": round((v[1] / 1e9) / (v[0] / 1000.0), 1) if v[0] > 0 else None}
+              for k, v in prof.items() if v[2] > 0}
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1) if achieved else None,
+                "peak": peak, "peak_kind": peak_kind + " hbm_gbs (STREAM-style copy)", "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                "algorithmic_bytes_per_launch": dbytes / dn if dn else None,
+                "path_frac_compulsory_5GB_per_hv": round(value / world * 5.0e9 / (peak * 1e9), 4)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": list(N128), "nt": NT,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2_policy": "inputs larger than L2: 4.0 GB of stored time states read per Hv"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes},
+        "gpu_launches": int(round(launches_per_hv * args.steps)),
+        "roofline": roofline,
+        "kernel_shares": shares,
+        "result_finite": finite,
+    }
+
+    # ---- plain FP64 method, same workload (a few Hv)
+    if not args.no_fp64 and rank == 0:
+        del h
+        torch.cuda.empty_cache()
+        prm64 = pkg.default_params(alpha=ALPHA, nt=NT)
+        h64 = pkg.Handle(N128, prm64, stream=stream, device=dev.index)
+        D = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+        g64 = h64.new_vec()
+        h64.lddmm_gradient(D(0.5 * v0t), I0.double(), I1.double(), g64, energy=False)
+        d64, hv64 = D(d), h64.new_vec()
+        h64.lddmm_hessvec(d64, hv64)
+        torch.cuda.synchronize(dev)
+        k64 = 3
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(k64):
+            h64.lddmm_hessvec(d64, hv64)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = a0.elapsed_time(a1) / k64
+        out["plain_fp64"] = {"value": 1000.0 / ms64, "unit": UNIT, "ms_per_hv": ms64, "steps": k64}
+        h64.close()
+        del h64
+        torch.cuda.empty_cache()
+        h = None
+
+    # ---- one full registration of the workload (FP32 form)
+    if args.registrations > 0 and rank == 0:
+        hr = pkg.Handle(N128, prm, stream=stream, device=dev.index)
+        lat = []
+        rep = None
+        for _ in range(args.registrations):
+            v = torch.zeros((3,) + N128, dtype=f32, device=dev)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rep = hr.lddmm_register(I0, I1, v)
+            torch.cuda.synchronize(dev)
+            lat.append(time.perf_counter() - t0)
+        hr.close()
+        lat.sort()
+        q = lambda p: lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
+        out["registration"] = {"registrations_per_s": len(lat) / sum(lat), "p50_s": q(0.5), "p99_s": q(0.99),
+                               "runs": len(lat), "gn_iters": rep["gn_iters"],
+                               "pcg_iters_total": rep["pcg_iters_total"], "mse_rel": rep["mse_rel"],
+                               "gnorm_rel": rep["gnorm_rel"], "jac_min": rep["jac_min"], "jac_max": rep["jac_max"],
+                               "status": rep["status"]}
+
+    # ---- CPU oracle on the host cores (bounded sample)
+    if not args.no_cpu and rank == 0:
+        cv, secs = oracle_hv_sample(P, v0t, d, stages=2)
+        out["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                               "host_cores": os.cpu_count(),
+                               "sample": f"FP64 NumPy oracle: 2 forward + 2 adjoint Jacobi stages at 128^3 "
+                                         f"({secs:.1f} s), scaled by 2*nt/2 = 10 to one Hv"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "native":
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        td.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_native(args, rank, world)
+    if world > 1 and args.impl == "native":
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -81,6 +81,9 @@ typedef struct {
     double pcg_rtol;     /* PCG relative residual tolerance                    */
     double armijo_c1;    /* Armijo sufficient-decrease constant                */
     int ls_maxit;        /* Armijo halvings before giving up                   */
+    int dealias;         /* 1 (default): 2/3-rule projector P on the products of
+                            the EPDiff and Jacobi equations, modes |k_a| <=
+                            (n_a - 1)/3 kept; 0: unfiltered products           */
 } lddmm_params;
 
 #define LDDMM_TRACE_MAX 64
@@ -99,7 +102,7 @@ typedef struct lddmm_handle lddmm_handle;
 
 /* Fill *p with the defaults: alpha 0.01, s 2, weight 1e-3, nt 10, cubic, V,
  * F64 compute and states, checkpoint 1, 5 GN x 10 PCG, rtol 0.1, c1 1e-4,
- * 10 halvings. */
+ * 10 halvings, dealiasing on. */
 void lddmm_default_params(lddmm_params *p);
 
 /* Device bytes that lddmm_create would allocate for (g, p); 0 if invalid.
@@ -119,8 +122,8 @@ lddmm_status lddmm_last_status(const lddmm_handle *h);
 lddmm_status lddmm_synchronize(lddmm_handle *h);
 
 /* Geodesic shooting (Sec. 2.2 EPDiff + Sec. 3 state equation): Heun steps of
- * dv/dt = -K ad*_v L v from v0, semi-Lagrangian transport of the inverse map
- * psi = x + u, m1 = I0(x + u1).
+ * dv/dt = -K P ad*_v L v from P v0, semi-Lagrangian transport of the inverse
+ * map psi = x + u, m1 = I0(x + u1).
  *   v0      [3][N]  initial velocity
  *   I0      [N]     source image (may be NULL when m1 is NULL)
  *   m1      [N]     out, warped source (nullable)
@@ -129,8 +132,9 @@ lddmm_status lddmm_synchronize(lddmm_handle *h);
 lddmm_status lddmm_shoot(lddmm_handle *h, const void *v0, const void *I0, void *m1, void *u1,
                          double *kinetic);
 
-/* Reduced gradient of E at v0 (Sec. 3: grad_{v1}E = lambda(1) grad m(1),
- * lambda(1) = -2 (m(1) - I1), carried back by the adjoint Jacobi equations).
+/* Reduced gradient of E(v0) = w <L v0, v0> + ||m1(P v0) - I1||^2 (Sec. 3:
+ * grad_{v1}E = lambda(1) grad m(1), lambda(1) = -2 (m(1) - I1), carried back
+ * by the adjoint Jacobi equations).
  *   grad   [3][N] out, g_V = K g_L2 (LDDMM_SPACE_V) or g_L2 (LDDMM_SPACE_L2)
  *   energy host [3] out (nullable; synchronises): E, data term, regulariser.
  * Stores the linearisation point (time states, grad m1) in the handle for
@@ -170,6 +174,17 @@ lddmm_status lddmm_jacobian_det(lddmm_handle *h, const void *u, void *J, double 
  * LDDMM_WARN_LINESEARCH (not sticky) when a line search failed. */
 lddmm_status lddmm_register(lddmm_handle *h, const void *I0, const void *I1, void *v0_inout,
                             lddmm_report *report);
+
+/* Optional kernel profiler (tracing; no counterpart in the paper).  When
+ * enabled, CUDA events bracket every kernel launch of the handle on its
+ * stream.  lddmm_profile_read returns, for one kernel class, the summed
+ * device time in ms, the algorithmic bytes (the compulsory reads + writes of
+ * each launch, counted from its arguments) and the number of launches since
+ * the last enable.  Enabling resets the counters; reading synchronises. */
+int lddmm_profile_num_classes(void);
+const char *lddmm_profile_class_name(int cls);
+lddmm_status lddmm_profile(lddmm_handle *h, int enable);
+lddmm_status lddmm_profile_read(lddmm_handle *h, int cls, double *ms, double *bytes, long long *launches);
 
 #ifdef __cplusplus
 }

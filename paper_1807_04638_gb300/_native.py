@@ -39,6 +39,7 @@ class lddmm_params(ctypes.Structure):
         ("compute_dtype", ctypes.c_int), ("state_dtype", ctypes.c_int),
         ("checkpoint_every", ctypes.c_int), ("gn_maxit", ctypes.c_int), ("pcg_maxit", ctypes.c_int),
         ("pcg_rtol", ctypes.c_double), ("armijo_c1", ctypes.c_double), ("ls_maxit", ctypes.c_int),
+        ("dealias", ctypes.c_int),
     ]
 
 
@@ -84,6 +85,10 @@ SIGNATURES = {
     "lddmm_apply_metric": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
     "lddmm_jacobian_det": (ctypes.c_int, [_P, _P, _P, _D]),
     "lddmm_register": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(lddmm_report)]),
+    "lddmm_profile_num_classes": (ctypes.c_int, []),
+    "lddmm_profile_class_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "lddmm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lddmm_profile_read": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, ctypes.POINTER(ctypes.c_longlong)]),
 }
 
 
@@ -234,6 +239,20 @@ class Handle:
             "mse_rel": rep.mse_rel, "gnorm_rel": rep.gnorm_rel, "jac_min": rep.jac_min, "jac_max": rep.jac_max,
             "energy": list(rep.energy[:k + 1]), "pcg_iters": list(rep.pcg_iters[:k]), "step": list(rep.step[:k]),
         }
+
+    def lddmm_profile(self, enable: bool):
+        _check(lib().lddmm_profile(self._h, 1 if enable else 0), "lddmm_profile")
+
+    def lddmm_profile_read(self):
+        """{kernel class: (device ms, algorithmic bytes, launches)} since enable."""
+        out = {}
+        L = lib()
+        for c in range(L.lddmm_profile_num_classes()):
+            ms, by, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+            _check(L.lddmm_profile_read(self._h, c, ctypes.byref(ms), ctypes.byref(by), ctypes.byref(n)),
+                   "lddmm_profile_read")
+            out[L.lddmm_profile_class_name(c).decode()] = (ms.value, by.value, n.value)
+        return out
 
     def lddmm_synchronize(self):
         _check(lib().lddmm_synchronize(self._h), "lddmm_synchronize")

@@ -21,6 +21,7 @@ static bool params_ok(const lddmm_params* p) {
     if (p->state_dtype != p->compute_dtype) return false;
     if (p->checkpoint_every != 1) return false;
     if (p->gn_maxit < 0 || p->pcg_maxit < 0 || p->ls_maxit < 1) return false;
+    if (p->dealias != 0 && p->dealias != 1) return false;
     return true;
 }
 
@@ -42,6 +43,7 @@ void lddmm_default_params(lddmm_params* p) {
     p->pcg_rtol = 0.1;
     p->armijo_c1 = 1e-4;
     p->ls_maxit = 10;
+    p->dealias = 1;
 }
 
 size_t lddmm_workspace_bytes(const lddmm_grid* g, const lddmm_params* p) {
@@ -144,6 +146,20 @@ lddmm_status lddmm_jacobian_det(lddmm_handle* h, const void* u, void* J, double*
 lddmm_status lddmm_register(lddmm_handle* h, const void* I0, const void* I1, void* v0_inout, lddmm_report* report) {
     if (!h || !h->eng) return LDDMM_ERR_ARG;
     return h->eng->reg(I0, I1, v0_inout, report);
+}
+
+int lddmm_profile_num_classes(void) { return KC_COUNT; }
+
+const char* lddmm_profile_class_name(int cls) { return cls >= 0 && cls < KC_COUNT ? kclass_names[cls] : ""; }
+
+lddmm_status lddmm_profile(lddmm_handle* h, int enable) {
+    if (!h || !h->eng) return LDDMM_ERR_ARG;
+    return h->eng->profile(enable);
+}
+
+lddmm_status lddmm_profile_read(lddmm_handle* h, int cls, double* ms, double* bytes, long long* launches) {
+    if (!h || !h->eng) return LDDMM_ERR_ARG;
+    return h->eng->profile_read(cls, ms, bytes, launches);
 }
 
 }  // extern "C"

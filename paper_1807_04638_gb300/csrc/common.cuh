@@ -30,12 +30,14 @@ template <class T> __device__ __forceinline__ cpx<T> rot(cpx<T> a, int dir) {
     return dir > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
 }
 
-// Spectral symbol: scale * L_hat^lpow * (i kappa_deriv, if deriv >= 0), with
-// L_hat = (1 + alpha |kappa|^2)^s and the Nyquist entry of i kappa zeroed.
+// Spectral symbol: scale * L_hat^lpow * (i kappa_deriv, if deriv >= 0)
+// [* P, if mask], with L_hat = (1 + alpha |kappa|^2)^s, the Nyquist entry of
+// i kappa zeroed and P the 2/3-rule band indicator |k_a| <= kcut_a.
 struct SymD {
     double scale;
     int lpow;
     int deriv;
+    int mask;
 };
 
 // Per-axis symbol tables on the device (length n0, n1, n2/2+1).
@@ -44,10 +46,17 @@ template <class T> struct SpecTabs {
     const T* ksq[3];  // kappa_a^2
     T alpha;
     int s;
+    int n[3];     // grid sizes (signed wave number of index k: k or k - n)
+    int kcut[3];  // band of the dealiasing projector P (n when dealiasing is off)
 };
 
 template <class T>
 __device__ __forceinline__ cpx<T> sym_apply(const SymD& sy, const SpecTabs<T>& tb, int k0, int k1, int k2, cpx<T> v) {
+    if (sy.mask) {
+        const int a0 = k0 <= tb.n[0] / 2 ? k0 : tb.n[0] - k0;
+        const int a1 = k1 <= tb.n[1] / 2 ? k1 : tb.n[1] - k1;
+        if (a0 > tb.kcut[0] || a1 > tb.kcut[1] || k2 > tb.kcut[2]) return mk((T)0, (T)0);
+    }
     T f = (T)sy.scale;
     if (sy.lpow != 0) {
         T base = (T)1 + tb.alpha * (tb.ksq[0][k0] + tb.ksq[1][k1] + tb.ksq[2][k2]);

@@ -29,8 +29,16 @@
 
 namespace lddmm {
 
+// Kernel classes for the optional CUDA-event profiler.
+enum KClass { KC_AX0 = 0, KC_AX1, KC_AX2, KC_ADSTAR, KC_TANPW, KC_ADJPW, KC_SL, KC_WARP, KC_RED, KC_SPEC, KC_MISC, KC_COUNT };
+static const char* const kclass_names[KC_COUNT] = {
+    "fft_axis0_c2c", "fft_axis1_c2c", "fft_axis2_r2c_c2r", "adstar_pointwise", "tangent_pointwise",
+    "adjoint_pointwise", "sl_map_step", "warp", "reduction", "spectral_combine", "misc_pointwise"};
+
 struct EngineBase {
     virtual ~EngineBase() {}
+    virtual lddmm_status profile(int enable) = 0;
+    virtual lddmm_status profile_read(int cls, double* ms, double* bytes, long long* launches) = 0;
     virtual lddmm_status shoot(const void* v0, const void* I0, void* m1, void* u1, double* kinetic) = 0;
     virtual lddmm_status gradient(const void* v0, const void* I0, const void* I1, void* grad, double* energy) = 0;
     virtual lddmm_status hessvec(const void* dv0, void* Hdv) = 0;
@@ -89,10 +97,10 @@ struct Layout {
 };
 inline Layout layout_for(const Dims& d, const lddmm_params* p, size_t tsize) {
     Layout L;
-    // pool + vhat(6) + v0hat(3) + R1(3) + tan(12) + tb(6) + adj(12) + adja(6) + dhat(3) + tmp(3)
-    L.spec_fields = POOL + 6 + 3 + 3 + 12 + 6 + 12 + 6 + 3 + 3;
-    // states + vfin(6) + u(6) + scratch + m1(1) + gm1(3) + r(1) + PCG (x r z p q g vt: 21)
-    L.real_fields = (size_t)2 * p->nt * 24 + 6 + 6 + RSCR + 1 + 3 + 1 + 21;
+    // pool + vhat(6) + v0hat(3) + v0full(3) + R1(3) + tan(12) + tb(6) + adj(12) + adja(6) + dhat(3) + tmp(3)
+    L.spec_fields = POOL + 6 + 3 + 3 + 3 + 12 + 6 + 12 + 6 + 3 + 3;
+    // states + vfin(6) + u(6) + scratch + m1(1) + gm1(3) + r(1) + Lv0(3) + PCG (x r z p q g vt: 21)
+    L.real_fields = (size_t)2 * p->nt * 24 + 6 + 6 + RSCR + 1 + 3 + 1 + 3 + 21;
     size_t b = L.spec_fields * d.NS * 2 * tsize + L.real_fields * d.N * tsize;
     b += (size_t)(d.n0 + d.n1 + d.n2) * 2 * tsize * 2;  // twiddles
     b += (size_t)(d.n0 + d.n1 + d.n2h) * tsize * 2;      // symbol tables
@@ -163,8 +171,8 @@ class Engine : public EngineBase {
 
     // device buffers
     C* pool[POOL];
-    C *vhat[2], *v0hat, *R1, *tan_[2], *tb, *adj[2], *adja, *dhat, *tmp;
-    T *states, *vfin, *ubuf[2], *rs, *m1, *gm1, *rbuf;
+    C *vhat[2], *v0hat, *v0full, *R1, *tan_[2], *tb, *adj[2], *adja, *dhat, *tmp;
+    T *states, *vfin, *ubuf[2], *rs, *m1, *gm1, *rbuf, *lv0;
     T *px, *pr, *pz, *pp, *pq, *pg, *pvt;
     double *partial, *dres, *hres = nullptr;
     FFTAxis ax[3];
@@ -174,9 +182,88 @@ class Engine : public EngineBase {
     int pool_top = 0;
     bool lin_valid = false;
 
+    // ---- optional kernel profiler: CUDA events around every launch
+    struct PendingEv {
+        int i0, i1, cls;
+        double bytes;
+    };
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    std::vector<PendingEv> pend;
+    double acc_ms[KC_COUNT] = {}, acc_bytes[KC_COUNT] = {};
+    long long acc_n[KC_COUNT] = {};
+
+    void prof_flush() {
+        if (pend.empty()) return;
+        cudaStreamSynchronize(st);
+        for (const PendingEv& q : pend) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[q.i0], ev[q.i1]);
+            acc_ms[q.cls] += ms;
+            acc_bytes[q.cls] += q.bytes;
+            acc_n[q.cls] += 1;
+        }
+        pend.clear();
+        ev_used = 0;
+    }
+    struct PScope {
+        Engine* e;
+        int cls, i0;
+        double bytes;
+        PScope(Engine* e_, int c, double b) : e(e_), cls(c), i0(-1), bytes(b) {
+            if (!e->prof_on) return;
+            if (e->ev_used + 2 > (int)e->ev.size()) e->prof_flush();
+            i0 = e->ev_used++;
+            cudaEventRecord(e->ev[i0], e->st);
+        }
+        ~PScope() {
+            if (i0 < 0) return;
+            const int i1 = e->ev_used++;
+            cudaEventRecord(e->ev[i1], e->st);
+            e->pend.push_back({i0, i1, cls, bytes});
+        }
+    };
+    lddmm_status profile(int enable) override {
+        if (enable) {
+            if (ev.empty()) {
+                ev.resize(8192);
+                for (auto& x : ev)
+                    if (cudaEventCreate(&x) != cudaSuccess) return fail(LDDMM_ERR_CUDA);
+            }
+            prof_flush();
+            for (int c = 0; c < KC_COUNT; ++c) acc_ms[c] = acc_bytes[c] = 0, acc_n[c] = 0;
+            prof_on = true;
+        } else {
+            prof_flush();
+            prof_on = false;
+        }
+        return status;
+    }
+    lddmm_status profile_read(int cls, double* ms, double* bytes, long long* launches) override {
+        if (cls < 0 || cls >= KC_COUNT) return LDDMM_ERR_ARG;
+        prof_flush();
+        if (ms) *ms = acc_ms[cls];
+        if (bytes) *bytes = acc_bytes[cls];
+        if (launches) *launches = acc_n[cls];
+        return status;
+    }
+    double pass_bytes(int axis, int sign, const PassParams<T>& q) const {
+        double b = 0;
+        const double sc = (double)d.NS * sizeof(C), sr = (double)d.N * sizeof(T);
+        for (int j = 0; j < q.njobs; ++j) {
+            const PassJob& jb = q.jobs[j];
+            if (axis < 2) b += (jb.nin + jb.nb + jb.nout) * sc;
+            else if (sign > 0) b += jb.nin * sc + jb.nout * sr;
+            else b += jb.nin * sr + sc;
+        }
+        return b;
+    }
+
     Engine(const Dims& dd, const lddmm_params& p, cudaStream_t s) : d(dd), prm(p), st(s) {}
 
     ~Engine() override {
+        for (auto& x : ev) cudaEventDestroy(x);
         if (base_) cudaFree(base_);
         if (hres) cudaFreeHost(hres);
     }
@@ -209,6 +296,7 @@ class Engine : public EngineBase {
         for (int i = 0; i < POOL; ++i) pool[i] = carve<C>(d.NS);
         for (int i = 0; i < 2; ++i) vhat[i] = carve<C>(3 * d.NS);
         v0hat = carve<C>(3 * d.NS);
+        v0full = carve<C>(3 * d.NS);
         R1 = carve<C>(3 * d.NS);
         for (int i = 0; i < 2; ++i) tan_[i] = carve<C>(6 * d.NS);
         tb = carve<C>(6 * d.NS);
@@ -223,6 +311,7 @@ class Engine : public EngineBase {
         m1 = carve<T>(d.N);
         gm1 = carve<T>(3 * d.N);
         rbuf = carve<T>(d.N);
+        lv0 = carve<T>(3 * d.N);
         px = carve<T>(3 * d.N);
         pr = carve<T>(3 * d.N);
         pz = carve<T>(3 * d.N);
@@ -271,6 +360,10 @@ class Engine : public EngineBase {
         }
         tabs.alpha = (T)prm.alpha;
         tabs.s = prm.s;
+        for (int a = 0; a < 3; ++a) {
+            tabs.n[a] = ns[a];
+            tabs.kcut[a] = prm.dealias ? (ns[a] - 1) / 3 : ns[a];
+        }
         if (off_ > cap_) return fail(LDDMM_ERR_OOM);
         // tile geometry
         const size_t budget = 150 * 1024;
@@ -323,19 +416,28 @@ class Engine : public EngineBase {
                 pp_.P = P2;
                 pp_.Ph = Ph2;
                 const int gx = (int)((d.rows + 2 * TL2 - 1) / (2 * TL2));
-                k_pass_axis2<T><<<dim3(gx, nj), FFT_THREADS, smem2, st>>>(pp_);
+                {
+                    PScope ps_(this, KC_AX2, pass_bytes(2, sign, pp_));
+                    k_pass_axis2<T><<<dim3(gx, nj), FFT_THREADS, smem2, st>>>(pp_);
+                }
             } else if (axis == 1) {
                 pp_.TL = TLc[1];
                 pp_.P = Pc[1];
                 pp_.Ph = 0;
                 const int gx = (int)(((size_t)d.n2h * d.n0 + TLc[1] - 1) / TLc[1]);
-                k_pass_c2c<T, 1><<<dim3(gx, nj), FFT_THREADS, smem_c[1], st>>>(pp_);
+                {
+                    PScope ps_(this, KC_AX1, pass_bytes(1, sign, pp_));
+                    k_pass_c2c<T, 1><<<dim3(gx, nj), FFT_THREADS, smem_c[1], st>>>(pp_);
+                }
             } else {
                 pp_.TL = TLc[0];
                 pp_.P = Pc[0];
                 pp_.Ph = 0;
                 const int gx = d.n2h * ((d.n1 + TLc[0] - 1) / TLc[0]);
-                k_pass_c2c<T, 0><<<dim3(gx, nj), FFT_THREADS, smem_c[0], st>>>(pp_);
+                {
+                    PScope ps_(this, KC_AX0, pass_bytes(0, sign, pp_));
+                    k_pass_c2c<T, 0><<<dim3(gx, nj), FFT_THREADS, smem_c[0], st>>>(pp_);
+                }
             }
         }
     }
@@ -345,12 +447,41 @@ class Engine : public EngineBase {
         memset(&j, 0, sizeof(j));
         return j;
     }
-    static SymD sym(double s, int l, int dv) {
+    static SymD sym(double s, int l, int dv, int mask = 0) {
         SymD y;
         y.scale = s;
         y.lpow = l;
         y.deriv = dv;
+        y.mask = mask;
         return y;
+    }
+    // out (3 spectral comps) = P in
+    void mask_copy(const C* in, C* out) {
+        for (int c = 0; c < 3; ++c) {
+            SpecComb<T> sc;
+            sc.nin = 1;
+            sc.in[0] = in + c * d.NS;
+            sc.sym[0] = sym(1.0, 0, -1, 1);
+            {
+                PScope ps_(this, KC_SPEC, 2.0 * d.NS * sizeof(C));
+                k_spec_comb<T><<<pw_grid(d.NS), PW_THREADS, 0, st>>>(sc, tabs, d.n0, d.n1, d.n2h, out + c * d.NS);
+            }
+        }
+    }
+    // slot = <L v0, v0> (regulariser of the energy), from F(v0) in v0full
+    void reg_async(const T* v0, int slot) {
+        std::vector<SpecLin> srcs;
+        std::vector<InvReq> reqs;
+        for (int c = 0; c < 3; ++c) {
+            SpecLin s;
+            s.n = 1;
+            s.p[0] = v0full + c * d.NS;
+            s.c[0] = 1.0;
+            srcs.push_back(s);
+            reqs.push_back({c, sym(1.0, 1, -1), lv0 + c * d.N});
+        }
+        inverse(srcs, reqs);
+        dot_async(lv0, v0, 3 * d.N, slot, d.cell);
     }
 
     // real_out = F^-1[ sym . lincomb(src) ]
@@ -361,6 +492,7 @@ class Engine : public EngineBase {
             int src, lpow;
             double scale;
             bool d0;
+            int mask;
             C* buf;
         };
         struct K1 {
@@ -376,10 +508,11 @@ class Engine : public EngineBase {
             const bool d0 = q.sym.deriv == 0;
             int f = -1;
             for (size_t i = 0; i < k0s.size(); ++i)
-                if (k0s[i].src == q.src && k0s[i].lpow == q.sym.lpow && k0s[i].scale == q.sym.scale && k0s[i].d0 == d0)
+                if (k0s[i].src == q.src && k0s[i].lpow == q.sym.lpow && k0s[i].scale == q.sym.scale &&
+                    k0s[i].d0 == d0 && k0s[i].mask == q.sym.mask)
                     f = (int)i;
             if (f < 0) {
-                k0s.push_back({q.src, q.sym.lpow, q.sym.scale, d0, palloc()});
+                k0s.push_back({q.src, q.sym.lpow, q.sym.scale, d0, q.sym.mask, palloc()});
                 f = (int)k0s.size() - 1;
             }
             r0[r] = f;
@@ -419,7 +552,7 @@ class Engine : public EngineBase {
                     setin();
                 }
                 j.out[j.nout] = k0s[i].buf;
-                j.osym[j.nout] = sym(k0s[i].scale * invN, k0s[i].lpow, k0s[i].d0 ? 0 : -1);
+                j.osym[j.nout] = sym(k0s[i].scale * invN, k0s[i].lpow, k0s[i].d0 ? 0 : -1, k0s[i].mask);
                 j.nout++;
             }
             flush();
@@ -473,7 +606,7 @@ class Engine : public EngineBase {
         struct G {
             int o, lpow;
             double scale;
-            int cls;
+            int cls, mask;
             C* buf;
             int nin;
         };
@@ -486,10 +619,10 @@ class Engine : public EngineBase {
                 int f = -1;
                 for (size_t i = 0; i < g2.size(); ++i)
                     if (g2[i].o == (int)o && g2[i].lpow == t.sym.lpow && g2[i].scale == t.sym.scale &&
-                        g2[i].cls == cls && g2[i].nin < MAXI)
+                        g2[i].cls == cls && g2[i].mask == t.sym.mask && g2[i].nin < MAXI)
                         f = (int)i;
                 if (f < 0) {
-                    g2.push_back({(int)o, t.sym.lpow, t.sym.scale, cls, palloc(), 0});
+                    g2.push_back({(int)o, t.sym.lpow, t.sym.scale, cls, t.sym.mask, palloc(), 0});
                     PassJob j = blank();
                     j.nout = 1;
                     j.out[0] = g2.back().buf;
@@ -512,10 +645,10 @@ class Engine : public EngineBase {
             int f = -1;
             for (size_t i = 0; i < g1.size(); ++i)
                 if (g1[i].o == a.o && g1[i].lpow == a.lpow && g1[i].scale == a.scale && g1[i].cls == cls0 &&
-                    g1[i].nin < MAXI)
+                    g1[i].mask == a.mask && g1[i].nin < MAXI)
                     f = (int)i;
             if (f < 0) {
-                g1.push_back({a.o, a.lpow, a.scale, cls0, palloc(), 0});
+                g1.push_back({a.o, a.lpow, a.scale, cls0, a.mask, palloc(), 0});
                 PassJob j = blank();
                 j.nout = 1;
                 j.out[0] = g1.back().buf;
@@ -542,7 +675,7 @@ class Engine : public EngineBase {
                     break;
                 }
                 j.in[j.nin] = a.buf;
-                j.isym[j.nin] = sym(a.scale, a.lpow, a.cls == 0 ? 0 : -1);
+                j.isym[j.nin] = sym(a.scale, a.lpow, a.cls == 0 ? 0 : -1, a.mask);
                 j.nin++;
             }
             for (auto& b : outs[o].bases) {
@@ -612,13 +745,25 @@ class Engine : public EngineBase {
 
     // ------------------------------------------------------------ reductions
     void dot_async(const T* a, const T* b, size_t n, int slot, double scale) {
-        k_dot_partial<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, partial);
-        k_finish<<<1, RED_THREADS, 0, st>>>(partial, RED_BLOCKS, 1, 0, 0, scale, dres + slot);
+        {
+            PScope ps_(this, KC_RED, (double)(b ? 2 : 1) * n * sizeof(T));
+            k_dot_partial<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, partial);
+        }
+        {
+            PScope ps_(this, KC_RED, 0.0);
+            k_finish<<<1, RED_THREADS, 0, st>>>(partial, RED_BLOCKS, 1, 0, 0, scale, dres + slot);
+        }
     }
     void minmax_async(const T* a, size_t n, int slot) {  // slots: max|a|, max a, min a
-        k_absmax_partial<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, n, partial);
+        {
+            PScope ps_(this, KC_RED, (double)n * sizeof(T));
+            k_absmax_partial<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, n, partial);
+        }
         for (int q = 0; q < 3; ++q)
-            k_finish<<<1, RED_THREADS, 0, st>>>(partial, RED_BLOCKS, 3, q, q == 2 ? 2 : 1, 1.0, dres + slot + q);
+            {
+                PScope ps_(this, KC_RED, 0.0);
+                k_finish<<<1, RED_THREADS, 0, st>>>(partial, RED_BLOCKS, 3, q, q == 2 ? 2 : 1, 1.0, dres + slot + q);
+            }
     }
     lddmm_status fetch(int first, int count) {
         LD_CK(cudaMemcpyAsync(hres + first, dres + first, count * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -644,7 +789,8 @@ class Engine : public EngineBase {
         const GridI gi{d.n0, d.n1, d.n2};
         const T ih0 = (T)(1.0 / d.h[0]), ih1 = (T)(1.0 / d.h[1]), ih2 = (T)(1.0 / d.h[2]);
         const int cubic = prm.interp == LDDMM_INTERP_CUBIC;
-        fwd_vec(v0, v0hat);
+        fwd_vec(v0, v0full);
+        mask_copy(v0full, v0hat);
         cudaMemsetAsync(ubuf[0], 0, 3 * d.N * sizeof(T), st);
         T* a = rs;
         for (int k = 0; k < nt; ++k) {
@@ -655,26 +801,35 @@ class Engine : public EngineBase {
             eval_fields({{cur, 1.0}}, S1);
             if (kinetic) dot_async(S1 + 12 * d.N, S1, 3 * d.N, k, d.cell);
             if (k >= 1)
-                k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, state(2 * (k - 1)), S1, ubuf[(k - 1) % 2],
-                                                                 ubuf[k % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
-            k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S1, d.N}, a, d.N);
+                {
+                    PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
+                    k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, state(2 * (k - 1)), S1, ubuf[(k - 1) % 2],
+                                                                     ubuf[k % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
+                }
+            {
+                PScope ps_(this, KC_ADSTAR, 27.0 * d.N * sizeof(T));
+                k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S1, d.N}, a, d.N);
+            }
             {
                 std::vector<FwdOut> outs(3);
                 for (int c = 0; c < 3; ++c) {
                     outs[c].out = R1 + c * d.NS;
-                    outs[c].terms.push_back({a + c * d.N, sym(-1.0, -1, -1)});
+                    outs[c].terms.push_back({a + c * d.N, sym(-1.0, -1, -1, 1)});
                 }
                 forward(outs);
             }
             // stage 2 at v*_k = v_k + dt R1
             T* S2 = state(2 * k + 1);
             eval_fields({{cur, 1.0}, {R1, dt_}}, S2);
-            k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S2, d.N}, a, d.N);
+            {
+                PScope ps_(this, KC_ADSTAR, 27.0 * d.N * sizeof(T));
+                k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S2, d.N}, a, d.N);
+            }
             {
                 std::vector<FwdOut> outs(3);
                 for (int c = 0; c < 3; ++c) {
                     outs[c].out = nxt + c * d.NS;
-                    outs[c].terms.push_back({a + c * d.N, sym(-0.5 * dt_, -1, -1)});
+                    outs[c].terms.push_back({a + c * d.N, sym(-0.5 * dt_, -1, -1, 1)});
                     outs[c].bases.push_back({cur + c * d.NS, 1.0});
                     outs[c].bases.push_back({R1 + c * d.NS, 0.5 * dt_});
                 }
@@ -697,15 +852,21 @@ class Engine : public EngineBase {
             inverse(srcs, reqs);
         }
         if (kinetic) dot_async(vfin + 3 * d.N, vfin, 3 * d.N, nt, d.cell);
-        k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, state(2 * (nt - 1)), vfin, ubuf[(nt - 1) % 2],
-                                                         ubuf[nt % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
+        {
+            PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
+            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, state(2 * (nt - 1)), vfin, ubuf[(nt - 1) % 2],
+                                                             ubuf[nt % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
+        }
     }
     T* u1() const { return ubuf[prm.nt % 2]; }
 
     void warp_and_grad(const T* I0) {
         const GridI gi{d.n0, d.n1, d.n2};
-        k_warp<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, I0, u1(), m1, (T)(1.0 / d.h[0]), (T)(1.0 / d.h[1]),
-                                                      (T)(1.0 / d.h[2]), prm.interp == LDDMM_INTERP_CUBIC, d.N);
+        {
+            PScope ps_(this, KC_WARP, 5.0 * d.N * sizeof(T));
+            k_warp<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, I0, u1(), m1, (T)(1.0 / d.h[0]), (T)(1.0 / d.h[1]),
+                                                          (T)(1.0 / d.h[2]), prm.interp == LDDMM_INTERP_CUBIC, d.N);
+        }
         std::vector<FwdOut> outs(1);
         outs[0].out = tmp;
         outs[0].terms.push_back({m1, sym(1.0, 0, -1)});
@@ -754,25 +915,28 @@ class Engine : public EngineBase {
                     for (int j = 0; j < 3; ++j) reqs.push_back({3 + c, sym(1.0, 0, j), X + (3 + 3 * c + j) * d.N});
                 }
                 inverse(srcs, reqs);
-                k_tangent_pw<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S, d.N}, StatePtr<T>{E, d.N}, X,
-                                                                    pq_, d.N);
+                {
+                    PScope ps_(this, KC_TANPW, 66.0 * d.N * sizeof(T));
+                    k_tangent_pw<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S, d.N}, StatePtr<T>{E, d.N}, X,
+                                                                        pq_, d.N);
+                }
                 std::vector<FwdOut> outs(6);
                 for (int c = 0; c < 3; ++c) {
                     FwdOut& oe = outs[c];
                     FwdOut& ox = outs[3 + c];
                     if (stg == 0) {
                         oe.out = be + c * d.NS;
-                        oe.terms.push_back({pq_ + c * d.N, sym(-1.0, -1, -1)});
+                        oe.terms.push_back({pq_ + c * d.N, sym(-1.0, -1, -1, 1)});
                         ox.out = bx + c * d.NS;
-                        ox.terms.push_back({pq_ + (3 + c) * d.N, sym(1.0, 0, -1)});
+                        ox.terms.push_back({pq_ + (3 + c) * d.N, sym(1.0, 0, -1, 1)});
                         ox.bases.push_back({ce + c * d.NS, 1.0});
                     } else {
                         oe.out = nxt + c * d.NS;
-                        oe.terms.push_back({pq_ + c * d.N, sym(-0.5 * dt_, -1, -1)});
+                        oe.terms.push_back({pq_ + c * d.N, sym(-0.5 * dt_, -1, -1, 1)});
                         oe.bases.push_back({ce + c * d.NS, 1.0});
                         oe.bases.push_back({be + c * d.NS, 0.5 * dt_});
                         ox.out = nxt + (3 + c) * d.NS;
-                        ox.terms.push_back({pq_ + (3 + c) * d.N, sym(0.5 * dt_, 0, -1)});
+                        ox.terms.push_back({pq_ + (3 + c) * d.N, sym(0.5 * dt_, 0, -1, 1)});
                         ox.bases.push_back({cx + c * d.NS, 1.0});
                         ox.bases.push_back({bx + c * d.NS, 0.5 * dt_});
                         ox.bases.push_back({ce + c * d.NS, 0.5 * dt_});
@@ -810,11 +974,14 @@ class Engine : public EngineBase {
                     else srcs.push_back(lin({{cx, 0.5 * dt_}, {axp, 0.5 * dt_ * dt_}}, c));
                 }
                 for (int c = 0; c < 3; ++c) {
-                    reqs.push_back({c, sym(1.0, -1, -1), Y + c * d.N});
-                    reqs.push_back({3 + c, sym(1.0, 0, -1), Y + (3 + c) * d.N});
+                    reqs.push_back({c, sym(1.0, -1, -1, 1), Y + c * d.N});
+                    reqs.push_back({3 + c, sym(1.0, 0, -1, 1), Y + (3 + c) * d.N});
                 }
                 inverse(srcs, reqs);
-                k_adjoint_pw<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S, d.N}, Y, G, d.N);
+                {
+                    PScope ps_(this, KC_ADJPW, 66.0 * d.N * sizeof(T));
+                    k_adjoint_pw<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S, d.N}, Y, G, d.N);
+                }
                 std::vector<FwdOut> outs(6);
                 for (int c = 0; c < 3; ++c) {
                     FwdOut& oe = outs[c];
@@ -865,7 +1032,10 @@ class Engine : public EngineBase {
                 sc.in[sc.nin] = B + c * d.NS;
                 sc.sym[sc.nin++] = sb;
             }
-            k_spec_comb<T><<<pw_grid(d.NS), PW_THREADS, 0, st>>>(sc, tabs, d.n0, d.n1, d.n2h, tmp + c * d.NS);
+            {
+                PScope ps_(this, KC_SPEC, (double)(sc.nin + 1) * d.NS * sizeof(C));
+                k_spec_comb<T><<<pw_grid(d.NS), PW_THREADS, 0, st>>>(sc, tabs, d.n0, d.n1, d.n2h, tmp + c * d.NS);
+            }
         }
         inv_vec(tmp, out);
     }
@@ -874,37 +1044,47 @@ class Engine : public EngineBase {
     void gradient_core(const T* v0, const T* I0, const T* I1, T* grad, int space) {
         shoot_core(v0, true);
         warp_and_grad(I0);
-        k_sub<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, rbuf, d.N);
+        {
+            PScope ps_(this, KC_MISC, 3.0 * d.N * sizeof(T));
+            k_sub<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, rbuf, d.N);
+        }
         dot_async(rbuf, nullptr, d.N, prm.nt + 2, d.cell);
-        k_final_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, gm1, nullptr, rs, 0, d.N);
+        reg_async(v0, prm.nt + 1);
+        {
+            PScope ps_(this, KC_MISC, 8.0 * d.N * sizeof(T));
+            k_final_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, gm1, nullptr, rs, 0, d.N);
+        }
         fwd_vec(rs, adj[0] + 3 * d.NS);
         cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
         adjoint_sweep();
         // g_L2 = 2 w L v0 + T^T b ;  V: K g_L2 = 2 w v0 + K T^T b
         const double w2 = 2.0 * prm.weight;
         if (space == LDDMM_SPACE_V)
-            spec_to_real2(v0hat, sym(w2, 0, -1), adj_result(), sym(1.0, -1, -1), grad);
+            spec_to_real2(v0full, sym(w2, 0, -1), adj_result(), sym(1.0, -1, -1, 1), grad);
         else
-            spec_to_real2(v0hat, sym(w2, 1, -1), adj_result(), sym(1.0, 0, -1), grad);
+            spec_to_real2(v0full, sym(w2, 1, -1), adj_result(), sym(1.0, 0, -1, 1), grad);
         lin_valid = true;
     }
     void hessvec_core(const T* dv0, T* out, int space) {
         fwd_vec(dv0, dhat);
-        cudaMemcpyAsync(tan_[0], dhat, 3 * d.NS * sizeof(C), cudaMemcpyDeviceToDevice, st);
+        mask_copy(dhat, tan_[0]);
         cudaMemsetAsync(tan_[0] + 3 * d.NS, 0, 3 * d.NS * sizeof(C), st);
         tangent_sweep();
         T* xi = rs;
         inv_vec(tan_[prm.nt % 2] + 3 * d.NS, xi);
         T* c = rs + 3 * d.N;
-        k_final_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, nullptr, gm1, xi, c, 1, d.N);
+        {
+            PScope ps_(this, KC_MISC, 8.0 * d.N * sizeof(T));
+            k_final_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, nullptr, gm1, xi, c, 1, d.N);
+        }
         fwd_vec(c, adj[0] + 3 * d.NS);
         cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
         adjoint_sweep();
         const double w2 = 2.0 * prm.weight;
         if (space == LDDMM_SPACE_V)
-            spec_to_real2(dhat, sym(w2, 0, -1), adj_result(), sym(1.0, -1, -1), out);
+            spec_to_real2(dhat, sym(w2, 0, -1), adj_result(), sym(1.0, -1, -1, 1), out);
         else
-            spec_to_real2(dhat, sym(w2, 1, -1), adj_result(), sym(1.0, 0, -1), out);
+            spec_to_real2(dhat, sym(w2, 1, -1), adj_result(), sym(1.0, 0, -1, 1), out);
     }
 
     // ------------------------------------------------------------ ABI operations
@@ -915,9 +1095,12 @@ class Engine : public EngineBase {
         lin_valid = false;
         if (m1o) {
             const GridI gi{d.n0, d.n1, d.n2};
-            k_warp<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, (const T*)I0, u1(), (T*)m1o, (T)(1.0 / d.h[0]),
-                                                          (T)(1.0 / d.h[1]), (T)(1.0 / d.h[2]),
-                                                          prm.interp == LDDMM_INTERP_CUBIC, d.N);
+            {
+                PScope ps_(this, KC_WARP, 5.0 * d.N * sizeof(T));
+                k_warp<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, (const T*)I0, u1(), (T*)m1o, (T)(1.0 / d.h[0]),
+                                                              (T)(1.0 / d.h[1]), (T)(1.0 / d.h[2]),
+                                                              prm.interp == LDDMM_INTERP_CUBIC, d.N);
+            }
         }
         if (u1o) cudaMemcpyAsync(u1o, u1(), 3 * d.N * sizeof(T), cudaMemcpyDeviceToDevice, st);
         if (check_launch() != LDDMM_OK) return status;
@@ -935,7 +1118,7 @@ class Engine : public EngineBase {
         if (check_launch() != LDDMM_OK) return status;
         if (energy) {
             if (fetch(0, prm.nt + 3) != LDDMM_OK) return status;
-            const double data = hres[prm.nt + 2], reg = prm.weight * hres[0];
+            const double data = hres[prm.nt + 2], reg = prm.weight * hres[prm.nt + 1];
             energy[0] = data + reg;
             energy[1] = data;
             energy[2] = reg;
@@ -956,7 +1139,8 @@ class Engine : public EngineBase {
         if (status != LDDMM_OK) return status;
         if (!dv0) return fail(LDDMM_ERR_ARG);
         if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
-        fwd_vec((const T*)dv0, tan_[0]);
+        fwd_vec((const T*)dv0, dhat);
+        mask_copy(dhat, tan_[0]);
         cudaMemsetAsync(tan_[0] + 3 * d.NS, 0, 3 * d.NS * sizeof(C), st);
         tangent_sweep();
         if (eta1) inv_vec(tan_[prm.nt % 2], (T*)eta1);
@@ -972,7 +1156,7 @@ class Engine : public EngineBase {
         if (beta) fwd_vec((const T*)beta, adj[0]);
         else cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
         adjoint_sweep();
-        inv_vec(adj_result(), (T*)out);
+        spec_to_real2(nullptr, sym(0.0, 0, -1), adj_result(), sym(1.0, 0, -1, 1), (T*)out);
         return check_launch();
     }
 
@@ -1005,7 +1189,10 @@ class Engine : public EngineBase {
             for (int j = 0; j < 3; ++j) reqs.push_back({c, sym(1.0, 0, j), rs + (3 * c + j) * d.N});
         }
         inverse(srcs, reqs);
-        k_jacdet<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(rs, J, d.N);
+        {
+            PScope ps_(this, KC_MISC, 10.0 * d.N * sizeof(T));
+            k_jacdet<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(rs, J, d.N);
+        }
     }
 
     lddmm_status jacobian_det(const void* u, void* J, double* minmax) override {
@@ -1032,12 +1219,19 @@ class Engine : public EngineBase {
         shoot_core(v, true);
         lin_valid = false;
         const GridI gi{d.n0, d.n1, d.n2};
-        k_warp<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, I0, u1(), m1, (T)(1.0 / d.h[0]), (T)(1.0 / d.h[1]),
-                                                      (T)(1.0 / d.h[2]), prm.interp == LDDMM_INTERP_CUBIC, d.N);
-        k_sub<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, rbuf, d.N);
+        {
+            PScope ps_(this, KC_WARP, 5.0 * d.N * sizeof(T));
+            k_warp<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, I0, u1(), m1, (T)(1.0 / d.h[0]), (T)(1.0 / d.h[1]),
+                                                          (T)(1.0 / d.h[2]), prm.interp == LDDMM_INTERP_CUBIC, d.N);
+        }
+        {
+            PScope ps_(this, KC_MISC, 3.0 * d.N * sizeof(T));
+            k_sub<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, rbuf, d.N);
+        }
         dot_async(rbuf, nullptr, d.N, prm.nt + 2, d.cell);
+        reg_async(v, prm.nt + 1);
         if (fetch(0, prm.nt + 3) != LDDMM_OK) return NAN;
-        return hres[prm.nt + 2] + prm.weight * hres[0];
+        return hres[prm.nt + 2] + prm.weight * hres[prm.nt + 1];
     }
 
     void kapply(const T* in, T* out) {  // out = K in (3 comps)
@@ -1062,7 +1256,7 @@ class Engine : public EngineBase {
         for (; it < maxit; ++it) {
             gradient_core(v, I0, I1, pg, LDDMM_SPACE_L2);
             if (fetch(0, prm.nt + 3) != LDDMM_OK) return status;
-            const double E = hres[prm.nt + 2] + prm.weight * hres[0];
+            const double E = hres[prm.nt + 2] + prm.weight * hres[prm.nt + 1];
             if (!std::isfinite(E)) return fail(LDDMM_ERR_NONFINITE);
             R.energy[it] = E;
             // |g|_inf in the chosen metric
@@ -1076,7 +1270,10 @@ class Engine : public EngineBase {
             if (it == 0) g0max = hres[60];
             // PCG on H x = -g, preconditioner K, x0 = 0
             cudaMemsetAsync(px, 0, n3 * sizeof(T), st);
-            k_lincomb2<T><<<g, PW_THREADS, 0, st>>>((T)-1, pg, (T)0, pg, pr, n3);
+            {
+                PScope ps_(this, KC_MISC, 3.0 * n3 * sizeof(T));
+                k_lincomb2<T><<<g, PW_THREADS, 0, st>>>((T)-1, pg, (T)0, pg, pr, n3);
+            }
             kapply(pr, pz);
             cudaMemcpyAsync(pp, pz, n3 * sizeof(T), cudaMemcpyDeviceToDevice, st);
             double rz = dot_now(pr, pz, n3);
@@ -1087,8 +1284,14 @@ class Engine : public EngineBase {
                 const double pq_ = dot_now(pp, pq, n3);
                 if (!(pq_ > 0.0)) break;
                 const double alpha = rz / pq_;
-                k_axpby<T><<<g, PW_THREADS, 0, st>>>((T)alpha, pp, (T)1, px, n3);
-                k_axpby<T><<<g, PW_THREADS, 0, st>>>((T)-alpha, pq, (T)1, pr, n3);
+                {
+                    PScope ps_(this, KC_MISC, 3.0 * n3 * sizeof(T));
+                    k_axpby<T><<<g, PW_THREADS, 0, st>>>((T)alpha, pp, (T)1, px, n3);
+                }
+                {
+                    PScope ps_(this, KC_MISC, 3.0 * n3 * sizeof(T));
+                    k_axpby<T><<<g, PW_THREADS, 0, st>>>((T)-alpha, pq, (T)1, pr, n3);
+                }
                 kapply(pr, pz);
                 const double rzn = dot_now(pr, pz, n3);
                 ++pit;
@@ -1096,7 +1299,10 @@ class Engine : public EngineBase {
                     prm.space == LDDMM_SPACE_V ? std::sqrt(std::max(rzn, 0.0)) : std::sqrt(dot_now(pr, pr, n3));
                 if (res <= prm.pcg_rtol * nrm0) break;
                 const double beta = rzn / rz;
-                k_axpby<T><<<g, PW_THREADS, 0, st>>>((T)1, pz, (T)beta, pp, n3);
+                {
+                    PScope ps_(this, KC_MISC, 3.0 * n3 * sizeof(T));
+                    k_axpby<T><<<g, PW_THREADS, 0, st>>>((T)1, pz, (T)beta, pp, n3);
+                }
                 rz = rzn;
             }
             R.pcg_iters[it] = pit;
@@ -1105,7 +1311,10 @@ class Engine : public EngineBase {
             double eps = 1.0;
             bool ok = false;
             for (int t = 0; t < prm.ls_maxit; ++t) {
-                k_lincomb2<T><<<g, PW_THREADS, 0, st>>>((T)1, v, (T)eps, px, pvt, n3);
+                {
+                    PScope ps_(this, KC_MISC, 3.0 * n3 * sizeof(T));
+                    k_lincomb2<T><<<g, PW_THREADS, 0, st>>>((T)1, v, (T)eps, px, pvt, n3);
+                }
                 const double Et = energy_at(pvt, I0, I1);
                 if (status != LDDMM_OK) return status;
                 if (std::isfinite(Et) && Et <= E + prm.armijo_c1 * eps * slope) {
@@ -1126,7 +1335,7 @@ class Engine : public EngineBase {
         // final metrics: energy, relative gradient, MSE_rel, Jacobian extrema
         gradient_core(v, I0, I1, pg, LDDMM_SPACE_L2);
         if (fetch(0, prm.nt + 3) != LDDMM_OK) return status;
-        R.energy[it] = hres[prm.nt + 2] + prm.weight * hres[0];
+        R.energy[it] = hres[prm.nt + 2] + prm.weight * hres[prm.nt + 1];
         const double data = hres[prm.nt + 2];
         const T* gsp = pg;
         if (prm.space == LDDMM_SPACE_V) {
@@ -1136,7 +1345,10 @@ class Engine : public EngineBase {
         minmax_async(gsp, n3, 60);
         if (fetch(60, 1) != LDDMM_OK) return status;
         R.gnorm_rel = g0max > 0 ? hres[60] / g0max : 0.0;
-        k_sub<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(I0, I1, rbuf, d.N);
+        {
+            PScope ps_(this, KC_MISC, 3.0 * d.N * sizeof(T));
+            k_sub<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(I0, I1, rbuf, d.N);
+        }
         const double d0 = dot_now(rbuf, nullptr, d.N);
         R.mse_rel = d0 > 0 ? data / d0 : 0.0;
         T* J = rs + 9 * d.N;

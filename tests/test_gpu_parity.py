@@ -198,3 +198,29 @@ def test_errors_are_reported(pkg):
         assert ei.value.status == 5
         with pytest.raises(TypeError):
             h.lddmm_shoot(torch.zeros((3,) + n, dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_unfiltered_products_option(pkg, prec):
+    """dealias = 0 reproduces the literal unfiltered scheme of the oracle."""
+    dtype, _ = DT[prec]
+    n = (20, 12, 18)
+    nt = 4
+    g = O.Grid(n, alpha=0.01, dealias=False)
+    I0, vtrue = synth.blob_pair_inputs(n, 6, kmax=2, max_disp_vox=1.0)
+    I0 = synth.spectral_gaussian_smooth(I0, 1.0)
+    I1 = O.shoot(g, vtrue, nt, I0).m1
+    p = O.Params(nt=nt)
+    v0 = 0.5 * vtrue
+    gl2, E, _, _, tr = O.gradient(g, p, v0, I0, I1)
+    d = synth.band_limited_field(n, synth.rng_for(8), 4.0, 3) * g.h[0]
+    hl2 = O.hessvec(g, p, tr, d)
+    tol = F64_TOL if prec == "f64" else 1e-5
+    with pkg.Handle(n, params(pkg, prec, nt=nt, dealias=0)) as h:
+        grad, hv = h.new_vec(), h.new_vec()
+        e = h.lddmm_gradient(dev(v0, dtype), dev(I0, dtype), dev(I1, dtype), grad)
+        h.lddmm_hessvec(dev(d, dtype), hv)
+        h.lddmm_synchronize()
+    assert abs(e[0] - E) < tol * abs(E)
+    assert rel(host(grad), O.to_space(g, p, gl2)) < tol
+    assert rel(host(hv), O.to_space(g, p, hl2)) < tol
