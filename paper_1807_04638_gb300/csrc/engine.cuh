@@ -19,10 +19,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
 #include "common.cuh"
+#include "fft_fast.cuh"
 #include "fft_kernels.cuh"
 #include "lddmm.h"
 #include "pw_kernels.cuh"
@@ -110,6 +112,13 @@ inline Layout layout_for(const Dims& d, const lddmm_params* p, size_t tsize) {
     return L;
 }
 
+// LDDMM_GENERIC_FFT=1 selects the generic (runtime-radix) passes for every
+// axis; used to cross-check the register-blocked passes.
+inline bool force_generic_fft() {
+    const char* e = getenv("LDDMM_GENERIC_FFT");
+    return e && e[0] == '1';
+}
+
 inline std::vector<int> radix_plan(int n) {
     std::vector<int> r;
     int m = n;
@@ -131,6 +140,48 @@ inline std::vector<int> radix_plan(int n) {
     }
     return r;
 }
+
+// Launch of the register-blocked passes for the compiled line lengths.
+template <class T> struct FastPass {
+    template <int N>
+    static bool go(int axis, int sign, PassParams<T>& pp, int nj, size_t rows, int n0, int n1, int n2h,
+                   cudaStream_t st, bool set_attr) {
+        (void)sign;
+        constexpr int TL = FAST_THREADS / (N / FastPlan<N>::E);
+        if (axis == 2) {
+            const size_t sm = fast_axis2_smem<T, N>();
+            if (set_attr) return cudaFuncSetAttribute(k_fast_axis2<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)sm) == cudaSuccess;
+            const int gx = (int)((rows + 2 * TL - 1) / (2 * TL));
+            k_fast_axis2<T, N><<<dim3(gx, nj), FAST_THREADS, sm, st>>>(pp);
+        } else if (axis == 1) {
+            const size_t sm = fast_c2c_smem<T, N>(1);
+            if (set_attr) return cudaFuncSetAttribute(k_fast_c2c<T, N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)sm) == cudaSuccess;
+            const int gx = (int)(((size_t)n2h * n0 + TL - 1) / TL);
+            k_fast_c2c<T, N, 1><<<dim3(gx, nj), FAST_THREADS, sm, st>>>(pp);
+        } else {
+            const size_t sm = fast_c2c_smem<T, N>(0);
+            if (set_attr) return cudaFuncSetAttribute(k_fast_c2c<T, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)sm) == cudaSuccess;
+            const int gx = n2h * ((n1 + TL - 1) / TL);
+            k_fast_c2c<T, N, 0><<<dim3(gx, nj), FAST_THREADS, sm, st>>>(pp);
+        }
+        return true;
+    }
+    // n: the line length of this axis.  Returns false when no plan exists.
+    static bool launch(int n, int axis, int sign, PassParams<T>& pp, int nj, size_t rows, int n0, int n1, int n2h,
+                       cudaStream_t st, bool set_attr = false) {
+        switch (n) {
+            case 32: return go<32>(axis, sign, pp, nj, rows, n0, n1, n2h, st, set_attr);
+            case 64: return go<64>(axis, sign, pp, nj, rows, n0, n1, n2h, st, set_attr);
+            case 128: return go<128>(axis, sign, pp, nj, rows, n0, n1, n2h, st, set_attr);
+            case 256: return go<256>(axis, sign, pp, nj, rows, n0, n1, n2h, st, set_attr);
+            default: return false;
+        }
+    }
+    static bool has(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
+};
 
 #define LD_CK(call)                                           \
     do {                                                      \
@@ -178,6 +229,7 @@ class Engine : public EngineBase {
     FFTAxis ax[3];
     SpecTabs<T> tabs;
     int TLc[2], Pc[2], TL2, P2, Ph2;
+    bool fast[3] = {false, false, false};
     size_t smem_c[2], smem2;
     int pool_top = 0;
     bool lin_valid = false;
@@ -382,6 +434,11 @@ class Engine : public EngineBase {
         LD_CK(cudaFuncSetAttribute(k_pass_c2c<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c[0]));
         LD_CK(cudaFuncSetAttribute(k_pass_c2c<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c[1]));
         LD_CK(cudaFuncSetAttribute(k_pass_axis2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+        for (int a = 0; a < 3; ++a) {
+            PassParams<T> dummy;
+            fast[a] = FastPass<T>::has(ns[a]) && !force_generic_fft() &&
+                      FastPass<T>::launch(ns[a], a, 0, dummy, 0, 0, 0, 0, 0, st, true);
+        }
         LD_CK(cudaDeviceSynchronize());
         return LDDMM_OK;
     }
@@ -411,7 +468,11 @@ class Engine : public EngineBase {
             pp_.tabs = tabs;
             pp_.njobs = nj;
             for (int j = 0; j < nj; ++j) pp_.jobs[j] = jobs[j0 + j];
-            if (axis == 2) {
+            if (fast[axis]) {
+                const int n = axis == 0 ? d.n0 : (axis == 1 ? d.n1 : d.n2);
+                PScope ps_(this, axis == 0 ? KC_AX0 : (axis == 1 ? KC_AX1 : KC_AX2), pass_bytes(axis, sign, pp_));
+                FastPass<T>::launch(n, axis, sign, pp_, nj, d.rows, d.n0, d.n1, d.n2h, st);
+            } else if (axis == 2) {
                 pp_.TL = TL2;
                 pp_.P = P2;
                 pp_.Ph = Ph2;

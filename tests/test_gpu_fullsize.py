@@ -1,0 +1,142 @@
+"""GPU parity at the sizes the benchmark runs (register-blocked FFT passes).
+
+* the metric operator and one gradient / Hessian product on 64^3 and mixed
+  power-of-two grids, element by element against the FP64 oracle;
+* the 128^3 workload in the benchmark's configuration (FP32 form, nt = 10,
+  alpha = 0.005): the shooting outputs against the oracle, and for the
+  Jacobi sweeps and the Gauss-Newton Hessian the properties that hold at any
+  size (exact transposition, symmetry), since one oracle Hv at 128^3 takes
+  minutes.
+"""
+import numpy as np
+import pytest
+
+from oracle import lddmm_oracle as O
+from paper_1807_04638_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1807_04638_gb300 as p
+    p.lib()
+    return p
+
+
+DT = {"f64": (torch.float64, 0), "f32": (torch.float32, 1)}
+
+
+def dev(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n", [(128, 128, 128), (64, 256, 32), (256, 32, 64)])
+def test_metric_large(pkg, prec, n):
+    dtype, cd = DT[prec]
+    g = O.Grid(n, alpha=0.005)
+    f = synth.rng_for(21).standard_normal((3,) + n)
+    tol = 1e-10 if prec == "f64" else 1e-5
+    with pkg.Handle(n, pkg.default_params(alpha=0.005, compute_dtype=cd, state_dtype=cd)) as h:
+        x = dev(f, dtype)
+        out = torch.empty_like(x)
+        h.lddmm_apply_metric(x, out, -1)
+        h.lddmm_synchronize()
+        assert rel(host(out), g.K(f)) < tol
+        h.lddmm_apply_metric(x, out, 2)
+        h.lddmm_synchronize()
+        assert rel(host(out), g.L(g.L(f))) < tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_gradient_hessvec_64(pkg, prec):
+    dtype, cd = DT[prec]
+    n = (64, 64, 64)
+    nt = 3
+    g = O.Grid(n, alpha=0.005)
+    I0, vtrue = synth.blob_pair_inputs(n, 31, kmax=3, max_disp_vox=2.0)
+    I0 = synth.spectral_gaussian_smooth(I0, 1.0)
+    I1 = O.shoot(g, vtrue, nt, I0).m1
+    p = O.Params(alpha=0.005, nt=nt)
+    v0 = 0.6 * vtrue
+    gl2, E, _, _, tr = O.gradient(g, p, v0, I0, I1)
+    d = synth.band_limited_field(n, synth.rng_for(32), 6.0, 3) * g.h[0]
+    hl2 = O.hessvec(g, p, tr, d)
+    tol = 1e-10 if prec == "f64" else 1e-5
+    with pkg.Handle(n, pkg.default_params(alpha=0.005, nt=nt, compute_dtype=cd, state_dtype=cd)) as h:
+        grad, hv = h.new_vec(), h.new_vec()
+        e = h.lddmm_gradient(dev(v0, dtype), dev(I0, dtype), dev(I1, dtype), grad)
+        h.lddmm_hessvec(dev(d, dtype), hv)
+        h.lddmm_synchronize()
+    assert abs(e[0] - E) < tol * abs(E)
+    assert rel(host(grad), O.to_space(g, p, gl2)) < tol
+    assert rel(host(hv), O.to_space(g, p, hl2)) < tol
+
+
+@pytest.fixture(scope="module")
+def workload128():
+    """The 128^3 benchmark workload (same recipe and seeds as bench.py)."""
+    import bench
+    return bench.workload_inputs()
+
+
+def test_shoot_128_bench_configuration(pkg, workload128):
+    P, v0t, e0, e1, d = workload128
+    n = (128, 128, 128)
+    g = O.Grid(n, alpha=0.005)
+    v0 = 0.5 * v0t
+    tr = O.shoot(g, v0, 10, P)
+    prm = pkg.default_params(alpha=0.005, nt=10, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32)
+    with pkg.Handle(n, prm) as h:
+        m1, u1 = h.new_img(), h.new_vec()
+        kin = h.lddmm_shoot(dev(v0, torch.float32), dev(P, torch.float32), m1, u1, kinetic=True)
+    assert rel(host(u1), tr.u) < 1e-5
+    assert rel(host(m1) - P, tr.m1 - P) < 1e-4
+    assert np.allclose(kin, tr.kinetic, rtol=1e-5, atol=0)
+
+
+def test_sweeps_and_hessian_properties_128(pkg, workload128):
+    P, v0t, e0, e1, d = workload128
+    n = (128, 128, 128)
+    r = synth.rng_for(40)
+    prm = pkg.default_params(alpha=0.005, nt=10, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32,
+                             space=pkg.LDDMM_SPACE_L2)
+    f32 = torch.float32
+    with pkg.Handle(n, prm) as h:
+        I0 = dev(P + e0, f32)
+        I1 = dev(np.roll(P, 3, axis=0) + e1, f32)
+        grad = h.new_vec()
+        e = h.lddmm_gradient(dev(0.5 * v0t, f32), I0, I1, grad)
+        assert np.isfinite(e).all()
+        x = dev(synth.band_limited_field(n, r, 20.0, 3), f32)
+        y = dev(synth.band_limited_field(n, r, 20.0, 3), f32)
+        be = dev(r.standard_normal((3,) + n), f32)
+        bx = dev(r.standard_normal((3,) + n), f32)
+        e1_, x1_, a0 = h.new_vec(), h.new_vec(), h.new_vec()
+        h.lddmm_jacobi_forward(x, e1_, x1_)
+        h.lddmm_jacobi_adjoint(be, bx, a0)
+        hx, hy = h.new_vec(), h.new_vec()
+        h.lddmm_hessvec(x, hx)
+        h.lddmm_hessvec(y, hy)
+        h.lddmm_synchronize()
+    X, Y = host(x), host(y)
+    lhs = np.sum(host(e1_) * host(be)) + np.sum(host(x1_) * host(bx))
+    rhs = np.sum(X * host(a0))
+    assert abs(lhs - rhs) < 1e-5 * (abs(lhs) + abs(rhs))
+    hxy, xhy = np.sum(host(hx) * Y), np.sum(X * host(hy))
+    assert abs(hxy - xhy) < 1e-5 * (abs(hxy) + abs(xhy))
+    assert np.sum(host(hx) * X) > 0 and np.isfinite(host(hx)).all()
