@@ -54,7 +54,8 @@ typedef enum {
     LDDMM_ERR_NONFINITE = 6,      /* NaN or Inf in an energy or a result       */
     LDDMM_ERR_DEVICE_CHECK = 7,   /* a device-side check recorded an error     */
     LDDMM_ERR_TIMEOUT = 8,        /* a host-side wait exceeded its limit       */
-    LDDMM_WARN_LINESEARCH = 9     /* Armijo search failed; registration stopped */
+    LDDMM_WARN_LINESEARCH = 9,    /* Armijo search failed; registration stopped */
+    LDDMM_ERR_TOO_LARGE = 10      /* grid exceeds lddmm_apply_metric_noalloc's scratch */
 } lddmm_status;
 
 enum { LDDMM_F64 = 0, LDDMM_F32 = 1, LDDMM_BF16 = 2 };          /* number types   */
@@ -185,6 +186,28 @@ int lddmm_profile_num_classes(void);
 const char *lddmm_profile_class_name(int cls);
 lddmm_status lddmm_profile(lddmm_handle *h, int enable);
 lddmm_status lddmm_profile_read(lddmm_handle *h, int cls, double *ms, double *bytes, long long *launches);
+
+/* Metric operator without device allocation (no counterpart in the paper).
+ * For callers that cannot call cudaMalloc -- code running while a CUDA graph
+ * is captured, real-time loops that must stay out of the allocator, plug-ins
+ * whose host application owns every device allocation -- and so cannot
+ * create a handle.  Computes out = L^power in (power -1 is K; L = (Id -
+ * alpha Lap)^s, no dealiasing) for `ncomp` scalar fields stored back to back
+ * on the grid g, in LDDMM_F64 or LDDMM_F32 (`dtype`), on `cuda_stream`.
+ * in / out are caller-owned device pointers; out may equal in.
+ * Scratch: a fixed static device array of lddmm_apply_metric_noalloc_capacity()
+ * bytes (24 MiB) compiled into the library; each GPU that loads the library
+ * holds it until the process exits.  A grid whose scratch need
+ * (lddmm_apply_metric_noalloc_scratch_bytes) exceeds it is rejected with
+ * LDDMM_ERR_TOO_LARGE before any device work (e.g. 128^3 fits in F32, not in
+ * F64).  The first call on each device looks up the array's device address
+ * (with that device current); make it before any stream capture.  Every call
+ * rewrites the scratch it reads; calls that overlap on the GPU share the one
+ * array and race.  Allocates nothing, host or device. */
+lddmm_status lddmm_apply_metric_noalloc(const lddmm_grid *g, double alpha, int s, int power, int dtype,
+                                        const void *in, void *out, int ncomp, void *cuda_stream);
+size_t lddmm_apply_metric_noalloc_scratch_bytes(const lddmm_grid *g, int dtype);
+size_t lddmm_apply_metric_noalloc_capacity(void);
 
 #ifdef __cplusplus
 }

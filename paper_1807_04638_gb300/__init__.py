@@ -7,5 +7,5 @@ library with ``python -m paper_1807_04638_gb300.build``.
 """
 from ._native import (  # noqa: F401
     LDDMM_F32, LDDMM_F64, LDDMM_INTERP_CUBIC, LDDMM_INTERP_LINEAR, LDDMM_SPACE_L2, LDDMM_SPACE_V,
-    Handle, LddmmError, default_params, lib, make_grid, workspace_bytes,
+    Handle, LddmmError, apply_metric_noalloc, default_params, lib, make_grid, workspace_bytes,
 )

@@ -24,6 +24,7 @@ STATUS = {
     0: "LDDMM_OK", 1: "LDDMM_ERR_ARG", 2: "LDDMM_ERR_SHAPE", 3: "LDDMM_ERR_OOM",
     4: "LDDMM_ERR_CUDA", 5: "LDDMM_ERR_NOT_LINEARIZED", 6: "LDDMM_ERR_NONFINITE",
     7: "LDDMM_ERR_DEVICE_CHECK", 8: "LDDMM_ERR_TIMEOUT", 9: "LDDMM_WARN_LINESEARCH",
+    10: "LDDMM_ERR_TOO_LARGE",
 }
 LDDMM_WARN_LINESEARCH = 9
 
@@ -89,6 +90,10 @@ SIGNATURES = {
     "lddmm_profile_class_name": (ctypes.c_char_p, [ctypes.c_int]),
     "lddmm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "lddmm_profile_read": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, ctypes.POINTER(ctypes.c_longlong)]),
+    "lddmm_apply_metric_noalloc": (ctypes.c_int, [ctypes.POINTER(lddmm_grid), ctypes.c_double, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "lddmm_apply_metric_noalloc_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(lddmm_grid), ctypes.c_int]),
+    "lddmm_apply_metric_noalloc_capacity": (ctypes.c_size_t, []),
 }
 
 
@@ -136,6 +141,29 @@ def _check(st: int, what: str, allow=()):
     if st != 0 and st not in allow:
         raise LddmmError(st, what)
     return st
+
+
+def apply_metric_noalloc(x, out, power, alpha, s=2, lengths=None, stream=None):
+    """out = L^power x through lddmm_apply_metric_noalloc (no device allocation).
+
+    x, out: contiguous CUDA tensors [ncomp, n0, n1, n2] (or [n0, n1, n2]) of
+    float64 or float32.  Raises LddmmError (LDDMM_ERR_TOO_LARGE) for grids
+    whose scratch exceeds the library's fixed array.
+    """
+    import torch
+    if x.dtype not in (torch.float64, torch.float32) or out.dtype != x.dtype:
+        raise TypeError("x and out must both be float64 or both float32")
+    if not (x.is_cuda and out.is_cuda and x.is_contiguous() and out.is_contiguous()) or x.shape != out.shape:
+        raise ValueError("x and out must be contiguous CUDA tensors of the same shape")
+    n = tuple(x.shape[-3:])
+    ncomp = x.numel() // math.prod(n)
+    g = make_grid(n, lengths)
+    st = stream if stream is not None else torch.cuda.current_stream(x.device)
+    dtype = LDDMM_F64 if x.dtype == torch.float64 else LDDMM_F32
+    with torch.cuda.device(x.device):
+        _check(lib().lddmm_apply_metric_noalloc(ctypes.byref(g), float(alpha), int(s), int(power), dtype,
+                                                _P(x.data_ptr()), _P(out.data_ptr()), ncomp,
+                                                _P(st.cuda_stream)), "lddmm_apply_metric_noalloc")
 
 
 class Handle:

@@ -96,6 +96,7 @@ const char* lddmm_status_string(lddmm_status s) {
         case LDDMM_ERR_DEVICE_CHECK: return "device-side or planner check failed";
         case LDDMM_ERR_TIMEOUT: return "host wait exceeded its limit";
         case LDDMM_WARN_LINESEARCH: return "Armijo line search failed; registration stopped early";
+        case LDDMM_ERR_TOO_LARGE: return "grid too large for the fixed scratch of lddmm_apply_metric_noalloc";
     }
     return "unknown status";
 }
