@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--registrations", type=int, default=1, help="full registrations to time (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--no-prof", action="store_true", help="skip the per-kernel profiled pass")
+    ap.add_argument("--n", type=int, default=128, help="cubic grid size (profiling runs; the metric is 128)")
+    ap.add_argument("--nt", type=int, default=NT, help="time steps (profiling runs; the metric uses 10)")
     return ap.parse_args()
 
 
@@ -108,6 +112,7 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- inputs
 def workload_inputs(n=N128, seed=1):
     """Phantom, true velocity and noise for the 128^3 workload (seeded)."""
+    n = tuple(n)
     from paper_1807_04638_gb300 import synth
     P, v0, e0, e1 = synth.ellipsoid_pair_inputs(n, seed, kmax=6, max_disp_vox=6.0, noise_sigma=0.02)
     d = synth.band_limited_field(n, synth.rng_for(seed + 1000), 6.0, 3) * (2 * 3.141592653589793 / n[0])
@@ -191,13 +196,14 @@ def run_native(args, rank, world):
         if dist:
             td.barrier()
 
-    P, v0t, e0, e1, d = workload_inputs()
+    NG = (args.n,) * 3
+    P, v0t, e0, e1, d = workload_inputs(NG)
     f32 = torch.float32
     T = lambda a, dt=f32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
-    prm = pkg.default_params(alpha=ALPHA, nt=NT, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32,
+    prm = pkg.default_params(alpha=ALPHA, nt=args.nt, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32,
                              gn_maxit=10, pcg_maxit=50, pcg_rtol=0.1)
     stream = torch.cuda.current_stream(dev)
-    h = pkg.Handle(N128, prm, stream=stream, device=dev.index)
+    h = pkg.Handle(NG, prm, stream=stream, device=dev.index)
     # target: phantom warped by the true velocity (library shoot), plus noise
     I0 = T(P + e0)
     m1 = h.new_img()
@@ -235,6 +241,38 @@ def run_native(args, rank, world):
     finite = bool(np.isfinite(hv_host).all())
 
     # ---- end to end through the public API with pinned host buffers
+    e2e_value, vec_bytes = None, 3 * int(np.prod(NG)) * 4
+    if not args.no_e2e:
+        e2e_value = e2e_run(args, h, d, hv, stream, dev, barrier, world, dist)
+    out_e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes}
+
+    # ---- kernel classes: CUDA events around every launch (separate pass)
+    roofline, shares, launches_per_hv = None, None, None
+    if not args.no_prof:
+        roofline, shares, launches_per_hv = profile_run(h, delta, hv, value, world)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if NG == N128 and args.nt == NT else f"{NG} nt={args.nt} profiling case",
+                   "n": list(NG), "nt": args.nt,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2_policy": "inputs larger than L2: 4.0 GB of stored time states read per Hv"},
+        "clocks": clocks,
+        "e2e": out_e2e,
+        "gpu_launches": int(round(launches_per_hv * args.steps)) if launches_per_hv else None,
+        "roofline": roofline,
+        "kernel_shares": shares,
+        "result_finite": finite,
+    }
+    return finish(args, out, h, v0t, d, I0, I1, stream, dev, rank, P, NG)
+
+
+def e2e_run(args, h, d, hv, stream, dev, barrier, world, dist):
+    import numpy as np
+    import torch
+    f32 = torch.float32
     hd = torch.tensor(np.ascontiguousarray(d), dtype=f32).pin_memory()
     ho = torch.empty_like(hd).pin_memory()
     dbuf = h.new_vec()
@@ -255,13 +293,14 @@ def run_native(args, rank, world):
     barrier()
     ems = ee0.elapsed_time(ee1)
     if dist:
+        import torch.distributed as td
         t = torch.tensor([ems], device=dev)
         td.all_reduce(t, op=td.ReduceOp.MAX)
         ems = float(t.item())
-    e2e_value = world * args.steps / (ems / 1000.0)
-    vec_bytes = 3 * int(np.prod(N128)) * 4
+    return world * args.steps / (ems / 1000.0)
 
-    # ---- kernel classes: CUDA events around every launch (separate pass)
+
+def profile_run(h, delta, hv, value, world):
     h.lddmm_profile(True)
     nprof = 3
     for _ in range(nprof):
@@ -282,28 +321,23 @@ def run_native(args, rank, world):
                 "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
                 "algorithmic_bytes_per_launch": dbytes / dn if dn else None,
                 "path_frac_compulsory_5GB_per_hv": round(value / world * 5.0e9 / (peak * 1e9), 4)}
+    return roofline, shares, launches_per_hv
 
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": list(N128), "nt": NT,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2_policy": "inputs larger than L2: 4.0 GB of stored time states read per Hv"},
-        "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes},
-        "gpu_launches": int(round(launches_per_hv * args.steps)),
-        "roofline": roofline,
-        "kernel_shares": shares,
-        "result_finite": finite,
-    }
+
+def finish(args, out, h, v0t, d, I0, I1, stream, dev, rank, P, NG):
+    import numpy as np
+    import torch
+
+    import paper_1807_04638_gb300 as pkg
+    f32 = torch.float32
+    prm = h.params
 
     # ---- plain FP64 method, same workload (a few Hv)
     if not args.no_fp64 and rank == 0:
-        del h
+        h.close()
         torch.cuda.empty_cache()
-        prm64 = pkg.default_params(alpha=ALPHA, nt=NT)
-        h64 = pkg.Handle(N128, prm64, stream=stream, device=dev.index)
+        prm64 = pkg.default_params(alpha=ALPHA, nt=args.nt)
+        h64 = pkg.Handle(NG, prm64, stream=stream, device=dev.index)
         D = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
         g64 = h64.new_vec()
         h64.lddmm_gradient(D(0.5 * v0t), I0.double(), I1.double(), g64, energy=False)
@@ -322,15 +356,14 @@ def run_native(args, rank, world):
         h64.close()
         del h64
         torch.cuda.empty_cache()
-        h = None
 
     # ---- one full registration of the workload (FP32 form)
     if args.registrations > 0 and rank == 0:
-        hr = pkg.Handle(N128, prm, stream=stream, device=dev.index)
+        hr = pkg.Handle(NG, prm, stream=stream, device=dev.index)
         lat = []
         rep = None
         for _ in range(args.registrations):
-            v = torch.zeros((3,) + N128, dtype=f32, device=dev)
+            v = torch.zeros((3,) + NG, dtype=f32, device=dev)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             rep = hr.lddmm_register(I0, I1, v)
@@ -346,7 +379,7 @@ def run_native(args, rank, world):
                                "status": rep["status"]}
 
     # ---- CPU oracle on the host cores (bounded sample)
-    if not args.no_cpu and rank == 0:
+    if not args.no_cpu and rank == 0 and tuple(NG) == N128:
         cv, secs = oracle_hv_sample(P, v0t, d, stages=2)
         out["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
                                "host_cores": os.cpu_count(),
