@@ -23,6 +23,10 @@ template <> struct FastPlan<128> { static constexpr bool ok = true; static const
 template <> struct FastPlan<256> { static constexpr bool ok = true; static constexpr int E = 8, RADS = 0x488; };
 
 constexpr int FAST_THREADS = 256;
+// Resident blocks per SM the register budget is sized for: 4 for FP32
+// (<= 64 registers), 2 for FP64, so that enough loads are in flight to hide
+// DRAM latency.
+template <class T> struct FastOcc { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
 
 template <class T> struct Rad8 {
     // y_k = sum_r x_r w^{rk}, w = e^{dir 2 pi i / 8}
@@ -116,7 +120,7 @@ __device__ __forceinline__ void fast_fft(cpx<T> (&x)[FastPlan<N>::E], cpx<T>* b0
 // AXIS 1: lines along k1 (contiguous), MAP 1: a warp covers 32/TPL lines.
 // AXIS 0: lines along k0 (stride n1), MAP 0: a warp covers TL columns.
 template <class T, int N, int AXIS>
-__global__ void __launch_bounds__(FAST_THREADS) k_fast_c2c(const __grid_constant__ PassParams<T> pp) {
+__global__ void __launch_bounds__(FAST_THREADS, FastOcc<T>::value) k_fast_c2c(const __grid_constant__ PassParams<T> pp) {
     constexpr int E = FastPlan<N>::E;
     constexpr int TPL = N / E;
     constexpr int TL = FAST_THREADS / TPL;
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(FAST_THREADS) k_fast_c2c(const __grid_constant
 // spectrum of the block is staged in H[row][k] (pitch Ph) for the transposed
 // [k2][row] spectral layout.
 template <class T, int N>
-__global__ void __launch_bounds__(FAST_THREADS) k_fast_axis2(const __grid_constant__ PassParams<T> pp) {
+__global__ void __launch_bounds__(FAST_THREADS, FastOcc<T>::value) k_fast_axis2(const __grid_constant__ PassParams<T> pp) {
     constexpr int E = FastPlan<N>::E;
     constexpr int TPL = N / E;
     constexpr int TL = FAST_THREADS / TPL;
