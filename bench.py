@@ -119,6 +119,23 @@ def workload_inputs(n=N128, seed=1):
     return P, v0, e0, e1, d
 
 
+# DRAM traffic per launch of the dominant kernel class, from an ncu capture
+# (profiles/hv_128cubed_f32_launch_list.md), valid only for the kernel sources
+# it was measured on: reported as null once the sources change.
+TRAFFIC = {"digest": "4b7f297702baefdc", "fft_axis2_r2c_c2r": 163.0e6}
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1807_04638_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -318,7 +335,9 @@ def profile_run(h, delta, hv, value, world):
               for k, v in prof.items() if v[2] > 0}
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1) if achieved else None,
                 "peak": peak, "peak_kind": peak_kind + " hbm_gbs (STREAM-style copy)", "unit": "GB/s",
-                "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                "frac": round(achieved / peak, 4) if achieved else None,
+                "traffic": TRAFFIC.get(dom) if TRAFFIC["digest"] == kernel_digest() else None,
+                "kernel_digest": kernel_digest(),
                 "algorithmic_bytes_per_launch": dbytes / dn if dn else None,
                 "path_frac_compulsory_5GB_per_hv": round(value / world * 5.0e9 / (peak * 1e9), 4)}
     return roofline, shares, launches_per_hv
