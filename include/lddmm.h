@@ -124,7 +124,9 @@ lddmm_status lddmm_synchronize(lddmm_handle *h);
 
 /* Geodesic shooting (Sec. 2.2 EPDiff + Sec. 3 state equation): Heun steps of
  * dv/dt = -K P ad*_v L v from P v0, semi-Lagrangian transport of the inverse
- * map psi = x + u, m1 = I0(x + u1).
+ * map psi = x + u, m1 = I0(x + u1).  With I0 != NULL the shoot also stores
+ * grad m1 and becomes the linearisation point of lddmm_shoot_vjp,
+ * lddmm_hessvec and lddmm_jacobi_*.
  *   v0      [3][N]  initial velocity
  *   I0      [N]     source image (may be NULL when m1 is NULL)
  *   m1      [N]     out, warped source (nullable)
@@ -148,6 +150,16 @@ lddmm_status lddmm_gradient(lddmm_handle *h, const void *v0, const void *I0, con
  * Gauss-Newton drops):  H dv0 = 2 w L dv0 + T^T [2 (grad m1 . xi1) grad m1],
  * returned in the metric of `space` (V: K H_L2).  dv0, Hdv [3][N]. */
 lddmm_status lddmm_hessvec(lddmm_handle *h, const void *dv0, void *Hdv);
+
+/* Vector-Jacobian product of the shooting map v0 -> m1 = I0 o phi_1^-1
+ * (reverse-mode derivative; Sec. 3: the gradient is computed at t = 1 and
+ * carried back by the adjoint Jacobi equations).  With the Jacobi-field
+ * linearisation delta m1 = -grad m1 . xi1,
+ *     out = P T^T (-G grad m1),
+ * the derivative of sum_x G(x) m1(x) with respect to v0 (sum pairing, no cell
+ * volume).  Valid at the last lddmm_gradient or lddmm_shoot with I0 != NULL;
+ * otherwise LDDMM_ERR_NOT_LINEARIZED.  G [N], out [3][N]. */
+lddmm_status lddmm_shoot_vjp(lddmm_handle *h, const void *G, void *out);
 
 /* Forward Jacobi (tangent) sweep T at the last gradient's v0: from
  * (eta0, xi0) = (dv0, 0) integrate eta' = R'(v) eta, xi' = eta + ad_v xi;

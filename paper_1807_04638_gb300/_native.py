@@ -81,6 +81,7 @@ SIGNATURES = {
     "lddmm_shoot": (ctypes.c_int, [_P, _P, _P, _P, _P, _D]),
     "lddmm_gradient": (ctypes.c_int, [_P, _P, _P, _P, _P, _D]),
     "lddmm_hessvec": (ctypes.c_int, [_P, _P, _P]),
+    "lddmm_shoot_vjp": (ctypes.c_int, [_P, _P, _P]),
     "lddmm_jacobi_forward": (ctypes.c_int, [_P, _P, _P, _P]),
     "lddmm_jacobi_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
     "lddmm_apply_metric": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
@@ -232,6 +233,10 @@ class Handle:
     def lddmm_hessvec(self, dv0, Hdv):
         _check(lib().lddmm_hessvec(self._h, self._ptr(dv0, self.vec_shape(), "dv0"),
                                    self._ptr(Hdv, self.vec_shape(), "Hdv")), "lddmm_hessvec")
+
+    def lddmm_shoot_vjp(self, G, out):
+        _check(lib().lddmm_shoot_vjp(self._h, self._ptr(G, self.n, "G"), self._ptr(out, self.vec_shape(), "out")),
+               "lddmm_shoot_vjp")
 
     def lddmm_jacobi_forward(self, dv0, eta1=None, xi1=None):
         _check(lib().lddmm_jacobi_forward(self._h, self._ptr(dv0, self.vec_shape(), "dv0"),

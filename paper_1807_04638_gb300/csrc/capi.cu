@@ -144,6 +144,11 @@ lddmm_status lddmm_jacobian_det(lddmm_handle* h, const void* u, void* J, double*
     return h->eng->jacobian_det(u, J, minmax);
 }
 
+lddmm_status lddmm_shoot_vjp(lddmm_handle* h, const void* G, void* out) {
+    if (!h || !h->eng) return LDDMM_ERR_ARG;
+    return h->eng->shoot_vjp(G, out);
+}
+
 lddmm_status lddmm_register(lddmm_handle* h, const void* I0, const void* I1, void* v0_inout, lddmm_report* report) {
     if (!h || !h->eng) return LDDMM_ERR_ARG;
     return h->eng->reg(I0, I1, v0_inout, report);

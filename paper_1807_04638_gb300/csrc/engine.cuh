@@ -50,6 +50,7 @@ struct EngineBase {
     virtual lddmm_status jacobian_det(const void* u, void* J, double* minmax) = 0;
     virtual lddmm_status reg(const void* I0, const void* I1, void* v0, lddmm_report* rep) = 0;
     virtual lddmm_status synchronize() = 0;
+    virtual lddmm_status shoot_vjp(const void* G, void* out) = 0;
     lddmm_status status = LDDMM_OK;
 };
 
@@ -1154,14 +1155,11 @@ class Engine : public EngineBase {
         if (!v0 || (m1o && !I0)) return fail(LDDMM_ERR_ARG);
         shoot_core((const T*)v0, kinetic != nullptr);
         lin_valid = false;
-        if (m1o) {
-            const GridI gi{d.n0, d.n1, d.n2};
-            {
-                PScope ps_(this, KC_WARP, 5.0 * d.N * sizeof(T));
-                k_warp<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, (const T*)I0, u1(), (T*)m1o, (T)(1.0 / d.h[0]),
-                                                              (T)(1.0 / d.h[1]), (T)(1.0 / d.h[2]),
-                                                              prm.interp == LDDMM_INTERP_CUBIC, d.N);
-            }
+        if (I0) {
+            // m1 and grad m1 make this shoot a linearisation point (lddmm_shoot_vjp, hessvec)
+            warp_and_grad((const T*)I0);
+            if (m1o) cudaMemcpyAsync(m1o, m1, d.N * sizeof(T), cudaMemcpyDeviceToDevice, st);
+            lin_valid = true;
         }
         if (u1o) cudaMemcpyAsync(u1o, u1(), 3 * d.N * sizeof(T), cudaMemcpyDeviceToDevice, st);
         if (check_launch() != LDDMM_OK) return status;
@@ -1267,6 +1265,23 @@ class Engine : public EngineBase {
             minmax[0] = hres[62];
             minmax[1] = hres[61];
         }
+        return check_launch();
+    }
+
+    // out = T^T (-G grad m1): the vector-Jacobian product of v0 -> m1 at the
+    // last linearisation point (Jacobi-field linearisation delta m1 = -grad m1 . xi1)
+    lddmm_status shoot_vjp(const void* G, void* out) override {
+        if (status != LDDMM_OK) return status;
+        if (!G || !out) return fail(LDDMM_ERR_ARG);
+        if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
+        {
+            PScope ps_(this, KC_MISC, 8.0 * d.N * sizeof(T));
+            k_vjp_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>((const T*)G, gm1, rs, d.N);
+        }
+        fwd_vec(rs, adj[0] + 3 * d.NS);
+        cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
+        adjoint_sweep();
+        spec_to_real2(nullptr, sym(0.0, 0, -1), adj_result(), sym(1.0, 0, -1, 1), (T*)out);
         return check_launch();
     }
 

@@ -338,6 +338,17 @@ __global__ void k_final_source(const T* __restrict__ m1, const T* __restrict__ I
     }
 }
 
+// Source of the shooting vector-Jacobian product: out_c = -G grad_c m1
+template <class T>
+__global__ void k_vjp_source(const T* __restrict__ G, const T* __restrict__ gm, T* __restrict__ out, size_t N) {
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        const T g = -G[x];
+        out[x] = g * gm[x];
+        out[N + x] = g * gm[N + x];
+        out[2 * N + x] = g * gm[2 * N + x];
+    }
+}
+
 // r = m1 - I1
 template <class T>
 __global__ void k_sub(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ r, size_t n) {
