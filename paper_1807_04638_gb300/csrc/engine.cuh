@@ -142,6 +142,21 @@ inline std::vector<int> radix_plan(int n) {
     return r;
 }
 
+// The dynamic shared-memory limit of a kernel is process-wide: every site that
+// raises it sets the device's opt-in maximum, so that a handle (or call) for a
+// smaller grid never lowers the limit under a concurrent launch of a larger one.
+inline int smem_optin_max() {
+    int dev = 0, v = 48 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+template <class K>
+inline bool raise_smem_limit(K kernel, size_t need) {
+    const int mx = smem_optin_max();
+    if ((size_t)mx < need) return false;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) == cudaSuccess;
+}
+
 // Launch of the register-blocked passes for the compiled line lengths.
 template <class T> struct FastPass {
     template <int N>
@@ -151,20 +166,17 @@ template <class T> struct FastPass {
         constexpr int TL = FAST_THREADS / (N / FastPlan<N>::E);
         if (axis == 2) {
             const size_t sm = fast_axis2_smem<T, N>();
-            if (set_attr) return cudaFuncSetAttribute(k_fast_axis2<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)sm) == cudaSuccess;
+            if (set_attr) return raise_smem_limit(k_fast_axis2<T, N>, sm);
             const int gx = (int)((rows + 2 * TL - 1) / (2 * TL));
             k_fast_axis2<T, N><<<dim3(gx, nj), FAST_THREADS, sm, st>>>(pp);
         } else if (axis == 1) {
             const size_t sm = fast_c2c_smem<T, N>(1);
-            if (set_attr) return cudaFuncSetAttribute(k_fast_c2c<T, N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)sm) == cudaSuccess;
+            if (set_attr) return raise_smem_limit(k_fast_c2c<T, N, 1>, sm);
             const int gx = (int)(((size_t)n2h * n0 + TL - 1) / TL);
             k_fast_c2c<T, N, 1><<<dim3(gx, nj), FAST_THREADS, sm, st>>>(pp);
         } else {
             const size_t sm = fast_c2c_smem<T, N>(0);
-            if (set_attr) return cudaFuncSetAttribute(k_fast_c2c<T, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)sm) == cudaSuccess;
+            if (set_attr) return raise_smem_limit(k_fast_c2c<T, N, 0>, sm);
             const int gx = n2h * ((n1 + TL - 1) / TL);
             k_fast_c2c<T, N, 0><<<dim3(gx, nj), FAST_THREADS, sm, st>>>(pp);
         }
@@ -432,9 +444,9 @@ class Engine : public EngineBase {
         TL2 = 16;
         while (TL2 > 1 && ((size_t)2 * TL2 * Ph2 + 2 * TL2 * P2) * sizeof(C) > budget) TL2 /= 2;
         smem2 = ((size_t)2 * TL2 * Ph2 + 2 * TL2 * P2) * sizeof(C);
-        LD_CK(cudaFuncSetAttribute(k_pass_c2c<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c[0]));
-        LD_CK(cudaFuncSetAttribute(k_pass_c2c<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c[1]));
-        LD_CK(cudaFuncSetAttribute(k_pass_axis2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+        if (!raise_smem_limit(k_pass_c2c<T, 0>, smem_c[0]) || !raise_smem_limit(k_pass_c2c<T, 1>, smem_c[1]) ||
+            !raise_smem_limit(k_pass_axis2<T>, smem2))
+            return fail(LDDMM_ERR_CUDA);
         for (int a = 0; a < 3; ++a) {
             PassParams<T> dummy;
             fast[a] = FastPass<T>::has(ns[a]) && !force_generic_fft() &&

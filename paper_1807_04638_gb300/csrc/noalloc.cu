@@ -142,11 +142,8 @@ static lddmm_status noalloc_run(const Dims& d, double alpha, int s, int power, c
         fast[a] = FastPass<T>::has(ns[a]) && !force_generic_fft() &&
                   FastPass<T>::launch(ns[a], a, 0, dummy, 0, 0, 0, 0, 0, st, true);
     }
-    if (cudaFuncSetAttribute(k_pass_c2c<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc[0]) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_pass_c2c<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc[1]) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_pass_axis2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2) != cudaSuccess)
+    if (!raise_smem_limit(k_pass_c2c<T, 0>, smc[0]) || !raise_smem_limit(k_pass_c2c<T, 1>, smc[1]) ||
+        !raise_smem_limit(k_pass_axis2<T>, sm2))
         return LDDMM_ERR_CUDA;
 
     auto one = [&](int axis, int sign, const void* src, void* dst, SymD sy) {
