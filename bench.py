@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-prof", action="store_true", help="skip the per-kernel profiled pass")
     ap.add_argument("--n", type=int, default=128, help="cubic grid size (profiling runs; the metric is 128)")
     ap.add_argument("--nt", type=int, default=NT, help="time steps (profiling runs; the metric uses 10)")
+    ap.add_argument("--serve-requests", type=int, default=8,
+                    help="requests of the serving trace (0: skip); the full serving workload is 256")
+    ap.add_argument("--serve-fp64", type=int, default=0,
+                    help="also run the first M serving requests serially with the plain FP64 method")
     return ap.parse_args()
 
 
@@ -143,6 +147,95 @@ def load_peaks():
         return float(pk["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- serving workload
+SERVE_SIZES = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (160, 192, 160)]
+
+
+def serve_trace_inputs(nreq, seed=100):
+    """Serving workload: exponential inter-arrival times (mean 0.25 s), grid
+    ~ U{64^3, 96^3, 128^3, 160x192x160}, phantom ~ U{blob, ellipsoid}, a true
+    velocity with the phantom's band and a peak displacement of n_min/20
+    voxels.  Returns per request (arrival, shape, phantom, v0_true, noise0,
+    noise1); targets are made by the caller's own shoot."""
+    import numpy as np
+    from paper_1807_04638_gb300 import synth
+    rng = synth.rng_for(seed)
+    t = 0.0
+    out = []
+    for i in range(nreq):
+        t += rng.exponential(0.25)
+        n = SERVE_SIZES[int(rng.integers(0, len(SERVE_SIZES)))]
+        kind = int(rng.integers(0, 2))
+        sub = synth.rng_for(seed * 1000 + i)
+        disp = min(n) / 20.0
+        if kind == 0:
+            P = synth.blob_phantom(n, sub)
+            v = synth.random_velocity(n, sub, 4, disp)
+        else:
+            P = synth.ellipsoid_phantom(n, sub)
+            v = synth.random_velocity(n, sub, 6, disp)
+        e0 = synth.noise(n, sub, 0.02)
+        e1 = synth.noise(n, sub, 0.02)
+        out.append((t, n, P, v, e0, e1))
+    return out
+
+
+def run_serving(args, dev):
+    """Serve the trace in the FP32 form through the continuous-batching server
+    (80 GB budget), optionally replay the first M requests serially in FP64."""
+    import numpy as np
+    import torch
+
+    import paper_1807_04638_gb300 as pkg
+    from paper_1807_04638_gb300.serve import Request, Server, latency_stats, serial
+    trace = serve_trace_inputs(args.serve_requests)
+    mk = lambda cd: pkg.default_params(alpha=ALPHA, nt=NT, compute_dtype=cd, state_dtype=cd, gn_maxit=8,
+                                       pcg_maxit=20, pcg_rtol=0.1)
+    p32 = mk(pkg.LDDMM_F32)
+    reqs = []
+    targets = {}
+    for i, (t, n, P, v, e0, e1) in enumerate(trace):  # targets with the library's own shoot (untimed)
+        if n not in targets:
+            targets[n] = pkg.Handle(n, p32, device=dev.index)
+        h = targets[n]
+        m1 = h.new_img()
+        T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+        h.lddmm_shoot(T(v), T(P), m1)
+        I1 = m1.double().cpu().numpy() + e1
+        reqs.append(Request(rid=i, I0=P + e0, I1=I1, params=p32, arrival=t))
+    for h in targets.values():
+        h.close()
+    torch.cuda.empty_cache()
+    srv = Server(budget_bytes=80e9, max_inflight=8, device=dev.index)
+    try:
+        res = srv.run_trace(reqs)
+    finally:
+        srv.close()
+    st = latency_stats(res)
+    out = {"requests": len(reqs), "budget_gb": 80, "offered_rate_per_s": 4.0,
+           "sizes": [list(r.I0.shape) for r in reqs],
+           "peak_inflight": srv.peak_inflight, "peak_workspace_gb": round(srv.peak_used / 1e9, 2),
+           "mse_rel_mean": float(np.mean([r.report["mse_rel"] for r in res if r.report])), **st}
+    if args.serve_fp64 > 0:
+        m = min(args.serve_fp64, len(reqs))
+        p64 = mk(pkg.LDDMM_F64)
+        sub = [Request(rid=r.rid, I0=r.I0, I1=r.I1, params=p64, arrival=0.0) for r in reqs[:m]]
+        t0 = time.perf_counter()
+        ser = serial(sub, device=dev.index)
+        wall = time.perf_counter() - t0
+        ok = [r for r in ser if r.report]
+        dm = [abs(a.report["mse_rel"] - b.report["mse_rel"]) / b.report["mse_rel"]
+              for a, b in zip(res[:m], ser) if a.report and b.report]
+        served_sub = [r for r in res[:m] if r.report]
+        out["plain_fp64_serial"] = {"requests": m, "registrations_per_s": len(ok) / wall,
+                                    "mean_latency_s": wall / max(len(ok), 1),
+                                    "mse_rel_mean": float(np.mean([r.report["mse_rel"] for r in ok])),
+                                    "served_fp32_mse_rel_mean_same_requests":
+                                        float(np.mean([r.report["mse_rel"] for r in served_sub])),
+                                    "max_rel_diff_mse_rel_vs_served": max(dm) if dm else None}
+    return out
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -396,6 +489,10 @@ def finish(args, out, h, v0t, d, I0, I1, stream, dev, rank, P, NG):
                                "pcg_iters_total": rep["pcg_iters_total"], "mse_rel": rep["mse_rel"],
                                "gnorm_rel": rep["gnorm_rel"], "jac_min": rep["jac_min"], "jac_max": rep["jac_max"],
                                "status": rep["status"]}
+
+    # ---- serving trace (continuous batching, mixed grid sizes)
+    if args.serve_requests > 0 and rank == 0:
+        out["serving"] = run_serving(args, dev)
 
     # ---- CPU oracle on the host cores (bounded sample)
     if not args.no_cpu and rank == 0 and tuple(NG) == N128:
