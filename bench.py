@@ -444,10 +444,35 @@ def finish(args, out, h, v0t, d, I0, I1, stream, dev, rank, P, NG):
     f32 = torch.float32
     prm = h.params
 
-    # ---- plain FP64 method, same workload (a few Hv)
+    # ---- precision form: the same Hv with bfloat16 stored states
     if not args.no_fp64 and rank == 0:
+        prmb = pkg.default_params(alpha=ALPHA, nt=args.nt, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_BF16)
         h.close()
         torch.cuda.empty_cache()
+        hb = pkg.Handle(NG, prmb, stream=stream, device=dev.index)
+        Tf = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=f32, device=dev)
+        gb = hb.new_vec()
+        hb.lddmm_gradient(Tf(0.5 * v0t), I0, I1, gb, energy=False)
+        db, hvb = Tf(d), hb.new_vec()
+        for _ in range(2):
+            hb.lddmm_hessvec(db, hvb)
+        torch.cuda.synchronize(dev)
+        kb = 5
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(kb):
+            hb.lddmm_hessvec(db, hvb)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        msb = b0.elapsed_time(b1) / kb
+        out["bf16_states"] = {"value": 1000.0 / msb, "unit": UNIT, "ms_per_hv": msb, "steps": kb,
+                              "workspace_gb": round(pkg.workspace_bytes(NG, prmb) / 1e9, 2),
+                              "fp32_states_workspace_gb": round(pkg.workspace_bytes(NG, prm) / 1e9, 2)}
+        hb.close()
+        torch.cuda.empty_cache()
+
+    # ---- plain FP64 method, same workload (a few Hv)
+    if not args.no_fp64 and rank == 0:
         prm64 = pkg.default_params(alpha=ALPHA, nt=args.nt)
         h64 = pkg.Handle(NG, prm64, stream=stream, device=dev.index)
         D = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)

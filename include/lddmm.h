@@ -75,7 +75,9 @@ typedef struct {
     int interp;          /* LDDMM_INTERP_*: Catmull-Rom (default) or trilinear */
     int space;           /* LDDMM_SPACE_*: gradient / Hv metric (Sec. 3, last paragraph) */
     int compute_dtype;   /* LDDMM_F64 or LDDMM_F32                             */
-    int state_dtype;     /* stored time states: must equal compute_dtype        */
+    int state_dtype;     /* stored time states: compute_dtype, or LDDMM_BF16 with
+                            LDDMM_F32 compute (the stage fields are evaluated in
+                            FP32 and stored rounded to bfloat16)              */
     int checkpoint_every;/* 1 = keep every time state (only value supported)   */
     int gn_maxit;        /* Gauss-Newton iterations of lddmm_register          */
     int pcg_maxit;       /* PCG iterations per Gauss-Newton step (cap)         */

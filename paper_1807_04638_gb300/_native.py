@@ -15,7 +15,7 @@ from typing import Optional, Sequence
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "liblddmm.so")
 
-LDDMM_F64, LDDMM_F32 = 0, 1
+LDDMM_F64, LDDMM_F32, LDDMM_BF16 = 0, 1, 2
 LDDMM_INTERP_CUBIC, LDDMM_INTERP_LINEAR = 0, 1
 LDDMM_SPACE_V, LDDMM_SPACE_L2 = 0, 1
 LDDMM_TRACE_MAX = 64

@@ -18,7 +18,9 @@ static bool params_ok(const lddmm_params* p) {
     if (p->interp != LDDMM_INTERP_CUBIC && p->interp != LDDMM_INTERP_LINEAR) return false;
     if (p->space != LDDMM_SPACE_V && p->space != LDDMM_SPACE_L2) return false;
     if (p->compute_dtype != LDDMM_F64 && p->compute_dtype != LDDMM_F32) return false;
-    if (p->state_dtype != p->compute_dtype) return false;
+    // stored states: the compute type, or bfloat16 with FP32 compute (precision form)
+    if (p->state_dtype != p->compute_dtype && !(p->compute_dtype == LDDMM_F32 && p->state_dtype == LDDMM_BF16))
+        return false;
     if (p->checkpoint_every != 1) return false;
     if (p->gn_maxit < 0 || p->pcg_maxit < 0 || p->ls_maxit < 1) return false;
     if (p->dealias != 0 && p->dealias != 1) return false;

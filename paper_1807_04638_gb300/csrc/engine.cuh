@@ -102,9 +102,12 @@ inline Layout layout_for(const Dims& d, const lddmm_params* p, size_t tsize) {
     Layout L;
     // pool + vhat(6) + v0hat(3) + v0full(3) + R1(3) + tan(12) + tb(6) + adj(12) + adja(6) + dhat(3) + tmp(3)
     L.spec_fields = POOL + 6 + 3 + 3 + 3 + 12 + 6 + 12 + 6 + 3 + 3;
-    // states + vfin(6) + u(6) + scratch + m1(1) + gm1(3) + r(1) + Lv0(3) + PCG (x r z p q g vt: 21)
-    L.real_fields = (size_t)2 * p->nt * 24 + 6 + 6 + RSCR + 1 + 3 + 1 + 3 + 21;
+    // vfin(6) + u(6) + scratch + m1(1) + gm1(3) + r(1) + Lv0(3) + PCG (x r z p q g vt: 21)
+    // + FP32 copies of the last two stage velocities when states are bfloat16 (6)
+    const bool bf16 = p->state_dtype == LDDMM_BF16;
+    L.real_fields = 6 + 6 + RSCR + 1 + 3 + 1 + 3 + 21 + (bf16 ? 6 : 0);
     size_t b = L.spec_fields * d.NS * 2 * tsize + L.real_fields * d.N * tsize;
+    b += (size_t)2 * p->nt * 24 * d.N * (bf16 ? 2 : tsize);  // stored time states
     b += (size_t)(d.n0 + d.n1 + d.n2) * 2 * tsize * 2;  // twiddles
     b += (size_t)(d.n0 + d.n1 + d.n2h) * tsize * 2;      // symbol tables
     b += (RED_BLOCKS * 3 + NSLOT) * sizeof(double);
@@ -236,7 +239,9 @@ class Engine : public EngineBase {
     // device buffers
     C* pool[POOL];
     C *vhat[2], *v0hat, *v0full, *R1, *tan_[2], *tb, *adj[2], *adja, *dhat, *tmp;
-    T *states, *vfin, *ubuf[2], *rs, *m1, *gm1, *rbuf, *lv0;
+    void* states;  // 2 nt stages x 24 fields, T or bfloat16
+    bool bf16 = false;
+    T *vfin, *ubuf[2], *rs, *m1, *gm1, *rbuf, *lv0, *vss[2] = {nullptr, nullptr};
     T *px, *pr, *pz, *pp, *pq, *pg, *pvt;
     double *partial, *dres, *hres = nullptr;
     FFTAxis ax[3];
@@ -369,7 +374,13 @@ class Engine : public EngineBase {
         adja = carve<C>(6 * d.NS);
         dhat = carve<C>(3 * d.NS);
         tmp = carve<C>(3 * d.NS);
-        states = carve<T>((size_t)2 * prm.nt * 24 * d.N);
+        bf16 = prm.state_dtype == LDDMM_BF16;
+        if (bf16) {
+            states = carve<__nv_bfloat16>((size_t)2 * prm.nt * 24 * d.N);
+            for (int i = 0; i < 2; ++i) vss[i] = carve<T>(3 * d.N);
+        } else {
+            states = carve<T>((size_t)2 * prm.nt * 24 * d.N);
+        }
         vfin = carve<T>(6 * d.N);
         for (int i = 0; i < 2; ++i) ubuf[i] = carve<T>(3 * d.N);
         rs = carve<T>((size_t)RSCR * d.N);
@@ -465,7 +476,9 @@ class Engine : public EngineBase {
         return pool[pool_top++];
     }
     int pw_grid(size_t n) const { return (int)std::min<size_t>((n + PW_THREADS - 1) / PW_THREADS, 152 * 16); }
-    T* state(int s) const { return states + (size_t)s * 24 * d.N; }
+    T* state(int s) const { return (T*)states + (size_t)s * 24 * d.N; }
+    __nv_bfloat16* state_bf(int s) const { return (__nv_bfloat16*)states + (size_t)s * 24 * d.N; }
+    double state_elem() const { return bf16 ? 2.0 : (double)sizeof(T); }
     double dt() const { return 1.0 / prm.nt; }
 
     void launch(int axis, int sign, std::vector<PassJob>& jobs) {
@@ -866,24 +879,32 @@ class Engine : public EngineBase {
         fwd_vec(v0, v0full);
         mask_copy(v0full, v0hat);
         cudaMemsetAsync(ubuf[0], 0, 3 * d.N * sizeof(T), st);
-        T* a = rs;
+        // Stage fields are evaluated in the compute type: straight into the
+        // state store, or into scratch when the store keeps bfloat16 (then
+        // k_adstar writes the rounded copy and FP32 velocities feed the map
+        // transport).
+        T* a = bf16 ? rs + 24 * d.N : rs;
+        const double adb = 27.0 * d.N * sizeof(T) + (bf16 ? 48.0 * d.N : 0.0);
         for (int k = 0; k < nt; ++k) {
             C* cur = k == 0 ? v0hat : vhat[k % 2];
             C* nxt = vhat[(k + 1) % 2];
             // stage 1 at v_k
-            T* S1 = state(2 * k);
+            T* S1 = bf16 ? rs : state(2 * k);
             eval_fields({{cur, 1.0}}, S1);
             if (kinetic) dot_async(S1 + 12 * d.N, S1, 3 * d.N, k, d.cell);
             if (k >= 1)
                 {
                     PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
-                    k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, state(2 * (k - 1)), S1, ubuf[(k - 1) % 2],
+                    const T* vprev = bf16 ? vss[(k - 1) % 2] : state(2 * (k - 1));
+                    k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vprev, S1, ubuf[(k - 1) % 2],
                                                                      ubuf[k % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
                 }
             {
-                PScope ps_(this, KC_ADSTAR, 27.0 * d.N * sizeof(T));
-                k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S1, d.N}, a, d.N);
+                PScope ps_(this, KC_ADSTAR, adb);
+                k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S1, d.N}, a, d.N,
+                                                                bf16 ? state_bf(2 * k) : nullptr);
             }
+            if (bf16) cudaMemcpyAsync(vss[k % 2], S1, 3 * d.N * sizeof(T), cudaMemcpyDeviceToDevice, st);
             {
                 std::vector<FwdOut> outs(3);
                 for (int c = 0; c < 3; ++c) {
@@ -893,11 +914,12 @@ class Engine : public EngineBase {
                 forward(outs);
             }
             // stage 2 at v*_k = v_k + dt R1
-            T* S2 = state(2 * k + 1);
+            T* S2 = bf16 ? rs : state(2 * k + 1);
             eval_fields({{cur, 1.0}, {R1, dt_}}, S2);
             {
-                PScope ps_(this, KC_ADSTAR, 27.0 * d.N * sizeof(T));
-                k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S2, d.N}, a, d.N);
+                PScope ps_(this, KC_ADSTAR, adb);
+                k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S2, d.N}, a, d.N,
+                                                                bf16 ? state_bf(2 * k + 1) : nullptr);
             }
             {
                 std::vector<FwdOut> outs(3);
@@ -928,8 +950,9 @@ class Engine : public EngineBase {
         if (kinetic) dot_async(vfin + 3 * d.N, vfin, 3 * d.N, nt, d.cell);
         {
             PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
-            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, state(2 * (nt - 1)), vfin, ubuf[(nt - 1) % 2],
-                                                             ubuf[nt % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
+            const T* vprev = bf16 ? vss[(nt - 1) % 2] : state(2 * (nt - 1));
+            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vprev, vfin, ubuf[(nt - 1) % 2], ubuf[nt % 2],
+                                                             (T)dt_, ih0, ih1, ih2, cubic, d.N);
         }
     }
     T* u1() const { return ubuf[prm.nt % 2]; }
@@ -969,7 +992,7 @@ class Engine : public EngineBase {
             C* be = tb;
             C* bx = tb + 3 * d.NS;
             for (int stg = 0; stg < 2; ++stg) {
-                const T* S = state(2 * k + stg);
+                const int sidx = 2 * k + stg;
                 std::vector<SpecLin> srcs;
                 std::vector<InvReq> reqs;
                 for (int c = 0; c < 3; ++c) {
@@ -990,9 +1013,13 @@ class Engine : public EngineBase {
                 }
                 inverse(srcs, reqs);
                 {
-                    PScope ps_(this, KC_TANPW, 66.0 * d.N * sizeof(T));
-                    k_tangent_pw<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S, d.N}, StatePtr<T>{E, d.N}, X,
-                                                                        pq_, d.N);
+                    PScope ps_(this, KC_TANPW, 24.0 * d.N * state_elem() + 42.0 * d.N * sizeof(T));
+                    if (bf16)
+                        k_tangent_pw<T, __nv_bfloat16><<<pw_grid(d.N), PW_THREADS, 0, st>>>(
+                            StatePtr<__nv_bfloat16>{state_bf(sidx), d.N}, StatePtr<T>{E, d.N}, X, pq_, d.N);
+                    else
+                        k_tangent_pw<T, T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{state(sidx), d.N},
+                                                                               StatePtr<T>{E, d.N}, X, pq_, d.N);
                 }
                 std::vector<FwdOut> outs(6);
                 for (int c = 0; c < 3; ++c) {
@@ -1036,7 +1063,7 @@ class Engine : public EngineBase {
             C* ae = adja;
             C* axp = adja + 3 * d.NS;
             for (int stg = 0; stg < 2; ++stg) {
-                const T* S = state(stg == 0 ? 2 * k + 1 : 2 * k);
+                const int sidx = stg == 0 ? 2 * k + 1 : 2 * k;
                 std::vector<SpecLin> srcs;
                 std::vector<InvReq> reqs;
                 for (int c = 0; c < 3; ++c) {
@@ -1053,8 +1080,12 @@ class Engine : public EngineBase {
                 }
                 inverse(srcs, reqs);
                 {
-                    PScope ps_(this, KC_ADJPW, 66.0 * d.N * sizeof(T));
-                    k_adjoint_pw<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S, d.N}, Y, G, d.N);
+                    PScope ps_(this, KC_ADJPW, 24.0 * d.N * state_elem() + 42.0 * d.N * sizeof(T));
+                    if (bf16)
+                        k_adjoint_pw<T, __nv_bfloat16><<<pw_grid(d.N), PW_THREADS, 0, st>>>(
+                            StatePtr<__nv_bfloat16>{state_bf(sidx), d.N}, Y, G, d.N);
+                    else
+                        k_adjoint_pw<T, T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{state(sidx), d.N}, Y, G, d.N);
                 }
                 std::vector<FwdOut> outs(6);
                 for (int c = 0; c < 3; ++c) {

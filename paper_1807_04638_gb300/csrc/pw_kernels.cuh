@@ -6,24 +6,33 @@
 //   [0..2]   v_c          [3 + 3c + j]  D_j v_c
 //   [12..14] m_c = (L v)_c [15 + 3c + j] D_j m_c
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace lddmm {
 
 constexpr int PW_THREADS = 256;
 
-template <class T> struct StatePtr {
-    const T* p;  // 24 fields, stride N
+// Stored values are T or bfloat16 (the precision form's state storage); they
+// are widened to the compute type on load.
+template <class T> __device__ __forceinline__ T widen(T x) { return x; }
+__device__ __forceinline__ float widen(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <class S> struct StatePtr {
+    const S* p;  // 24 fields, stride N
     size_t N;
-    __device__ __forceinline__ T v(int c, size_t x) const { return p[c * N + x]; }
-    __device__ __forceinline__ T Dv(int c, int j, size_t x) const { return p[(3 + 3 * c + j) * N + x]; }
-    __device__ __forceinline__ T m(int c, size_t x) const { return p[(12 + c) * N + x]; }
-    __device__ __forceinline__ T Dm(int c, int j, size_t x) const { return p[(15 + 3 * c + j) * N + x]; }
+    __device__ __forceinline__ auto v(int c, size_t x) const { return widen(p[c * N + x]); }
+    __device__ __forceinline__ auto Dv(int c, int j, size_t x) const { return widen(p[(3 + 3 * c + j) * N + x]); }
+    __device__ __forceinline__ auto m(int c, size_t x) const { return widen(p[(12 + c) * N + x]); }
+    __device__ __forceinline__ auto Dm(int c, int j, size_t x) const { return widen(p[(15 + 3 * c + j) * N + x]); }
 };
 
-// ad*_v m = (Dv)^T m + (Dm) v + m div v  (EPDiff bracket, Sec. 2.2)
+// ad*_v m = (Dv)^T m + (Dm) v + m div v  (EPDiff bracket, Sec. 2.2).
+// With store != nullptr the 24 input fields are also written to the state
+// store in bfloat16 (precision form).
 template <class T>
-__global__ void k_adstar(StatePtr<T> S, T* __restrict__ out, size_t N) {
+__global__ void k_adstar(StatePtr<T> S, T* __restrict__ out, size_t N, __nv_bfloat16* __restrict__ store) {
     for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
         T v[3], m[3], Dv[3][3], Dm[3][3];
 #pragma unroll
@@ -44,6 +53,18 @@ __global__ void k_adstar(StatePtr<T> S, T* __restrict__ out, size_t N) {
             for (int j = 0; j < 3; ++j) a += Dv[j][i] * m[j] + Dm[i][j] * v[j];
             out[i * N + x] = a;
         }
+        if (store) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                store[c * N + x] = __float2bfloat16_rn((float)v[c]);
+                store[(12 + c) * N + x] = __float2bfloat16_rn((float)m[c]);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    store[(3 + 3 * c + j) * N + x] = __float2bfloat16_rn((float)Dv[c][j]);
+                    store[(15 + 3 * c + j) * N + x] = __float2bfloat16_rn((float)Dm[c][j]);
+                }
+            }
+        }
     }
 }
 
@@ -51,8 +72,8 @@ __global__ void k_adstar(StatePtr<T> S, T* __restrict__ out, size_t N) {
 //  p = ad*_eta m + ad*_v mu  (mu = L eta),   q = ad_v xi = (Dv) xi - (Dxi) v.
 // E holds eta in the 24-field state layout (eta, D eta, mu, D mu);
 // X holds xi (0..2) and D_j xi_c at 3 + 3c + j.
-template <class T>
-__global__ void k_tangent_pw(StatePtr<T> S, StatePtr<T> E, const T* __restrict__ X, T* __restrict__ out, size_t N) {
+template <class T, class SS>
+__global__ void k_tangent_pw(StatePtr<SS> S, StatePtr<T> E, const T* __restrict__ X, T* __restrict__ out, size_t N) {
     for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
         T v[3], m[3], e[3], mu[3], xi[3];
 #pragma unroll
@@ -87,8 +108,8 @@ __global__ void k_tangent_pw(StatePtr<T> S, StatePtr<T> E, const T* __restrict__
 //   group c     : R'^T part without L:  s = -sum_i D_c m_i y_i,  f_i = m_c y_i + delta_ic (m.y)
 //   group 3 + c : R'^T part under -L:   s = sum_i D_i v_c y_i + (div v) y_c,  f_j = -v_j y_c
 //   group 6 + c : ad_v^T yx:            s = sum_i D_c v_i yx_i,  f_j = v_j yx_c
-template <class T>
-__global__ void k_adjoint_pw(StatePtr<T> S, const T* __restrict__ Y, T* __restrict__ out, size_t N) {
+template <class T, class SS>
+__global__ void k_adjoint_pw(StatePtr<SS> S, const T* __restrict__ Y, T* __restrict__ out, size_t N) {
     for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
         T v[3], m[3], y[3], yx[3];
 #pragma unroll
