@@ -78,7 +78,11 @@ typedef struct {
     int state_dtype;     /* stored time states: compute_dtype, or LDDMM_BF16 with
                             LDDMM_F32 compute (the stage fields are evaluated in
                             FP32 and stored rounded to bfloat16)              */
-    int checkpoint_every;/* 1 = keep every time state (only value supported)   */
+    int checkpoint_every;/* 1: keep the fields of every Heun stage; c > 1: keep
+                            the spectral velocity every c steps and re-shoot
+                            one segment of c steps inside each sweep (memory of
+                            c steps' states instead of nt, one more shoot per
+                            sweep; the answer is unchanged)                   */
     int gn_maxit;        /* Gauss-Newton iterations of lddmm_register          */
     int pcg_maxit;       /* PCG iterations per Gauss-Newton step (cap)         */
     double pcg_rtol;     /* PCG relative residual tolerance                    */

@@ -21,7 +21,7 @@ static bool params_ok(const lddmm_params* p) {
     // stored states: the compute type, or bfloat16 with FP32 compute (precision form)
     if (p->state_dtype != p->compute_dtype && !(p->compute_dtype == LDDMM_F32 && p->state_dtype == LDDMM_BF16))
         return false;
-    if (p->checkpoint_every != 1) return false;
+    if (p->checkpoint_every < 1) return false;
     if (p->gn_maxit < 0 || p->pcg_maxit < 0 || p->ls_maxit < 1) return false;
     if (p->dealias != 0 && p->dealias != 1) return false;
     return true;

@@ -103,11 +103,16 @@ inline Layout layout_for(const Dims& d, const lddmm_params* p, size_t tsize) {
     // pool + vhat(6) + v0hat(3) + v0full(3) + R1(3) + tan(12) + tb(6) + adj(12) + adja(6) + dhat(3) + tmp(3)
     L.spec_fields = POOL + 6 + 3 + 3 + 3 + 12 + 6 + 12 + 6 + 3 + 3;
     // vfin(6) + u(6) + scratch + m1(1) + gm1(3) + r(1) + Lv0(3) + PCG (x r z p q g vt: 21)
-    // + FP32 copies of the last two stage velocities when states are bfloat16 (6)
+    // + FP32 copies of the last two stage-1 velocities for the map transport (6)
     const bool bf16 = p->state_dtype == LDDMM_BF16;
-    L.real_fields = 6 + 6 + RSCR + 1 + 3 + 1 + 3 + 21 + (bf16 ? 6 : 0);
+    const int cpe = p->checkpoint_every <= 1 ? p->nt : std::min(p->checkpoint_every, p->nt);
+    const bool ckpt = cpe < p->nt;
+    const int nseg = (p->nt + cpe - 1) / cpe;
+    L.real_fields = 6 + 6 + RSCR + 1 + 3 + 1 + 3 + 21 + 6;
+    if (ckpt) L.spec_fields += (size_t)3 * nseg;  // spectral v at the checkpoints
     size_t b = L.spec_fields * d.NS * 2 * tsize + L.real_fields * d.N * tsize;
-    b += (size_t)2 * p->nt * 24 * d.N * (bf16 ? 2 : tsize);  // stored time states
+    // stored time states: every stage, or one segment of checkpoint_every steps
+    b += (size_t)2 * (ckpt ? cpe : p->nt) * 24 * d.N * (bf16 ? 2 : tsize);
     b += (size_t)(d.n0 + d.n1 + d.n2) * 2 * tsize * 2;  // twiddles
     b += (size_t)(d.n0 + d.n1 + d.n2h) * tsize * 2;      // symbol tables
     b += (RED_BLOCKS * 3 + NSLOT) * sizeof(double);
@@ -239,8 +244,12 @@ class Engine : public EngineBase {
     // device buffers
     C* pool[POOL];
     C *vhat[2], *v0hat, *v0full, *R1, *tan_[2], *tb, *adj[2], *adja, *dhat, *tmp;
-    void* states;  // 2 nt stages x 24 fields, T or bfloat16
+    void* states;  // 2 nt stages (or 2 checkpoint_every stages) x 24 fields, T or bfloat16
     bool bf16 = false;
+    // checkpointing: v-hat kept every cpe steps, states of one segment resident
+    int cpe = 1, nseg = 1, seg_res = -1;
+    bool ckpt = false;
+    C* cps = nullptr;
     T *vfin, *ubuf[2], *rs, *m1, *gm1, *rbuf, *lv0, *vss[2] = {nullptr, nullptr};
     T *px, *pr, *pz, *pp, *pq, *pg, *pvt;
     double *partial, *dres, *hres = nullptr;
@@ -375,12 +384,14 @@ class Engine : public EngineBase {
         dhat = carve<C>(3 * d.NS);
         tmp = carve<C>(3 * d.NS);
         bf16 = prm.state_dtype == LDDMM_BF16;
-        if (bf16) {
-            states = carve<__nv_bfloat16>((size_t)2 * prm.nt * 24 * d.N);
-            for (int i = 0; i < 2; ++i) vss[i] = carve<T>(3 * d.N);
-        } else {
-            states = carve<T>((size_t)2 * prm.nt * 24 * d.N);
-        }
+        cpe = prm.checkpoint_every <= 1 ? prm.nt : std::min(prm.checkpoint_every, prm.nt);
+        ckpt = cpe < prm.nt;
+        nseg = (prm.nt + cpe - 1) / cpe;
+        const size_t nstate = (size_t)2 * (ckpt ? cpe : prm.nt) * 24 * d.N;
+        if (bf16) states = carve<__nv_bfloat16>(nstate);
+        else states = carve<T>(nstate);
+        for (int i = 0; i < 2; ++i) vss[i] = carve<T>(3 * d.N);
+        if (ckpt) cps = carve<C>((size_t)3 * nseg * d.NS);
         vfin = carve<T>(6 * d.N);
         for (int i = 0; i < 2; ++i) ubuf[i] = carve<T>(3 * d.N);
         rs = carve<T>((size_t)RSCR * d.N);
@@ -476,8 +487,18 @@ class Engine : public EngineBase {
         return pool[pool_top++];
     }
     int pw_grid(size_t n) const { return (int)std::min<size_t>((n + PW_THREADS - 1) / PW_THREADS, 152 * 16); }
-    T* state(int s) const { return (T*)states + (size_t)s * 24 * d.N; }
-    __nv_bfloat16* state_bf(int s) const { return (__nv_bfloat16*)states + (size_t)s * 24 * d.N; }
+    // element offset of global stage s in the state store (the resident
+    // segment's local index under checkpointing)
+    size_t sofs(int s) const {
+        const int l = ckpt ? s - 2 * cpe * seg_res : s;
+        if (l < 0 || l >= 2 * (ckpt ? cpe : prm.nt)) {
+            const_cast<Engine*>(this)->fail(LDDMM_ERR_DEVICE_CHECK);
+            return 0;
+        }
+        return (size_t)l * 24 * d.N;
+    }
+    T* state(int s) const { return (T*)states + sofs(s); }
+    __nv_bfloat16* state_bf(int s) const { return (__nv_bfloat16*)states + sofs(s); }
     double state_elem() const { return bf16 ? 2.0 : (double)sizeof(T); }
     double dt() const { return 1.0 / prm.nt; }
 
@@ -869,7 +890,75 @@ class Engine : public EngineBase {
     }
 
     // ------------------------------------------------------------ shooting
-    // v0 real -> stores every stage's fields, u1 in ubuf[nt%2], kinetic in dres[0..nt]
+    // One Heun step of the EPDiff shooting from `cur` into `nxt`, storing the
+    // fields of both stages.  With `transport` the semi-Lagrangian map step
+    // k-1 -> k runs too (its velocities are the FP32 copies in vss).
+    void shoot_step(int k, const C* cur, C* nxt, bool transport, bool kinetic) {
+        const double dt_ = dt();
+        const GridI gi{d.n0, d.n1, d.n2};
+        const T ih0 = (T)(1.0 / d.h[0]), ih1 = (T)(1.0 / d.h[1]), ih2 = (T)(1.0 / d.h[2]);
+        const int cubic = prm.interp == LDDMM_INTERP_CUBIC;
+        // Stage fields are evaluated in the compute type: straight into the
+        // state store, or into scratch when the store keeps bfloat16 (then
+        // k_adstar writes the rounded copy).
+        T* a = bf16 ? rs + 24 * d.N : rs;
+        const double adb = 27.0 * d.N * sizeof(T) + (bf16 ? 48.0 * d.N : 0.0);
+        // stage 1 at v_k
+        T* S1 = bf16 ? rs : state(2 * k);
+        eval_fields({{cur, 1.0}}, S1);
+        if (kinetic) dot_async(S1 + 12 * d.N, S1, 3 * d.N, k, d.cell);
+        if (transport && k >= 1) {
+            PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
+            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vss[(k - 1) % 2], S1, ubuf[(k - 1) % 2], ubuf[k % 2],
+                                                             (T)dt_, ih0, ih1, ih2, cubic, d.N);
+        }
+        {
+            PScope ps_(this, KC_ADSTAR, adb);
+            k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S1, d.N}, a, d.N,
+                                                            bf16 ? state_bf(2 * k) : nullptr);
+        }
+        if (transport) cudaMemcpyAsync(vss[k % 2], S1, 3 * d.N * sizeof(T), cudaMemcpyDeviceToDevice, st);
+        {
+            std::vector<FwdOut> outs(3);
+            for (int c = 0; c < 3; ++c) {
+                outs[c].out = R1 + c * d.NS;
+                outs[c].terms.push_back({a + c * d.N, sym(-1.0, -1, -1, 1)});
+            }
+            forward(outs);
+        }
+        // stage 2 at v*_k = v_k + dt R1
+        T* S2 = bf16 ? rs : state(2 * k + 1);
+        eval_fields({{cur, 1.0}, {R1, dt_}}, S2);
+        {
+            PScope ps_(this, KC_ADSTAR, adb);
+            k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S2, d.N}, a, d.N,
+                                                            bf16 ? state_bf(2 * k + 1) : nullptr);
+        }
+        {
+            std::vector<FwdOut> outs(3);
+            for (int c = 0; c < 3; ++c) {
+                outs[c].out = nxt + c * d.NS;
+                outs[c].terms.push_back({a + c * d.N, sym(-0.5 * dt_, -1, -1, 1)});
+                outs[c].bases.push_back({cur + c * d.NS, 1.0});
+                outs[c].bases.push_back({R1 + c * d.NS, 0.5 * dt_});
+            }
+            forward(outs);
+        }
+    }
+
+    // Make the states of segment j resident (checkpointing): re-shoot its
+    // steps from the stored spectral velocity of its first step.
+    void ensure_segment(int j) {
+        if (!ckpt || seg_res == j) return;
+        seg_res = j;
+        const int k0 = j * cpe, k1 = std::min(prm.nt, k0 + cpe);
+        for (int k = k0; k < k1; ++k) {
+            const C* cur = k == k0 ? cps + (size_t)j * 3 * d.NS : vhat[k % 2];
+            shoot_step(k, cur, vhat[(k + 1) % 2], false, false);
+        }
+    }
+
+    // v0 real -> stores the stage fields, u1 in ubuf[nt%2], kinetic in dres[0..nt]
     void shoot_core(const T* v0, bool kinetic) {
         const double dt_ = dt();
         const int nt = prm.nt;
@@ -879,58 +968,15 @@ class Engine : public EngineBase {
         fwd_vec(v0, v0full);
         mask_copy(v0full, v0hat);
         cudaMemsetAsync(ubuf[0], 0, 3 * d.N * sizeof(T), st);
-        // Stage fields are evaluated in the compute type: straight into the
-        // state store, or into scratch when the store keeps bfloat16 (then
-        // k_adstar writes the rounded copy and FP32 velocities feed the map
-        // transport).
-        T* a = bf16 ? rs + 24 * d.N : rs;
-        const double adb = 27.0 * d.N * sizeof(T) + (bf16 ? 48.0 * d.N : 0.0);
         for (int k = 0; k < nt; ++k) {
             C* cur = k == 0 ? v0hat : vhat[k % 2];
             C* nxt = vhat[(k + 1) % 2];
-            // stage 1 at v_k
-            T* S1 = bf16 ? rs : state(2 * k);
-            eval_fields({{cur, 1.0}}, S1);
-            if (kinetic) dot_async(S1 + 12 * d.N, S1, 3 * d.N, k, d.cell);
-            if (k >= 1)
-                {
-                    PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
-                    const T* vprev = bf16 ? vss[(k - 1) % 2] : state(2 * (k - 1));
-                    k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vprev, S1, ubuf[(k - 1) % 2],
-                                                                     ubuf[k % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
-                }
-            {
-                PScope ps_(this, KC_ADSTAR, adb);
-                k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S1, d.N}, a, d.N,
-                                                                bf16 ? state_bf(2 * k) : nullptr);
+            if (ckpt && k % cpe == 0) {
+                cudaMemcpyAsync(cps + (size_t)(k / cpe) * 3 * d.NS, cur, 3 * d.NS * sizeof(C),
+                                cudaMemcpyDeviceToDevice, st);
+                seg_res = k / cpe;
             }
-            if (bf16) cudaMemcpyAsync(vss[k % 2], S1, 3 * d.N * sizeof(T), cudaMemcpyDeviceToDevice, st);
-            {
-                std::vector<FwdOut> outs(3);
-                for (int c = 0; c < 3; ++c) {
-                    outs[c].out = R1 + c * d.NS;
-                    outs[c].terms.push_back({a + c * d.N, sym(-1.0, -1, -1, 1)});
-                }
-                forward(outs);
-            }
-            // stage 2 at v*_k = v_k + dt R1
-            T* S2 = bf16 ? rs : state(2 * k + 1);
-            eval_fields({{cur, 1.0}, {R1, dt_}}, S2);
-            {
-                PScope ps_(this, KC_ADSTAR, adb);
-                k_adstar<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{S2, d.N}, a, d.N,
-                                                                bf16 ? state_bf(2 * k + 1) : nullptr);
-            }
-            {
-                std::vector<FwdOut> outs(3);
-                for (int c = 0; c < 3; ++c) {
-                    outs[c].out = nxt + c * d.NS;
-                    outs[c].terms.push_back({a + c * d.N, sym(-0.5 * dt_, -1, -1, 1)});
-                    outs[c].bases.push_back({cur + c * d.NS, 1.0});
-                    outs[c].bases.push_back({R1 + c * d.NS, 0.5 * dt_});
-                }
-                forward(outs);
-            }
+            shoot_step(k, cur, nxt, true, kinetic);
         }
         // v_nt, m_nt in real space, last map step
         {
@@ -950,9 +996,8 @@ class Engine : public EngineBase {
         if (kinetic) dot_async(vfin + 3 * d.N, vfin, 3 * d.N, nt, d.cell);
         {
             PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
-            const T* vprev = bf16 ? vss[(nt - 1) % 2] : state(2 * (nt - 1));
-            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vprev, vfin, ubuf[(nt - 1) % 2], ubuf[nt % 2],
-                                                             (T)dt_, ih0, ih1, ih2, cubic, d.N);
+            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vss[(nt - 1) % 2], vfin, ubuf[(nt - 1) % 2],
+                                                             ubuf[nt % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
         }
     }
     T* u1() const { return ubuf[prm.nt % 2]; }
@@ -985,6 +1030,7 @@ class Engine : public EngineBase {
         T* X = rs + 24 * d.N;       // 12 fields
         T* pq_ = rs + 36 * d.N;     // 6 fields
         for (int k = 0; k < prm.nt; ++k) {
+            ensure_segment(k / cpe);
             C* cur = tan_[k % 2];
             C* nxt = tan_[(k + 1) % 2];
             C* ce = cur;
@@ -1056,6 +1102,7 @@ class Engine : public EngineBase {
         T* G = rs + 6 * d.N;    // 36 fields
         int cur_i = 0;
         for (int k = prm.nt - 1; k >= 0; --k) {
+            ensure_segment(k / cpe);
             C* cur = adj[cur_i];
             C* nxt = adj[1 - cur_i];
             C* ce = cur;

@@ -82,3 +82,57 @@ def test_bf16_states_128_bench_configuration(pkg):
             out.append((grad.double().cpu().numpy(), hv.double().cpu().numpy()))
     assert rel(out[1][0], out[0][0]) < 1e-2
     assert rel(out[1][1], out[0][1]) < 1e-2
+
+
+@pytest.mark.parametrize("cd,sd", [("f64", "f64"), ("f32", "f32"), ("f32", "bf16")])
+def test_checkpointing_recomputes_the_same_states(pkg, cd, sd):
+    """checkpoint_every = c keeps spectral velocities every c steps and
+    re-shoots segments inside the sweeps: gradient and Hv equal those of the
+    fully stored run."""
+    n, nt = (24, 20, 18), 7
+    dmap = {"f64": pkg.LDDMM_F64, "f32": pkg.LDDMM_F32, "bf16": pkg.LDDMM_BF16}
+    dt = torch.float64 if cd == "f64" else torch.float32
+    I0, vtrue = synth.blob_pair_inputs(n, 23, kmax=2, max_disp_vox=1.5)
+    I0 = synth.spectral_gaussian_smooth(I0, 1.0)
+    I1 = np.roll(I0, 2, axis=1)
+    d = synth.band_limited_field(n, synth.rng_for(24), 4.0, 3)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    outs = []
+    for c in (1, 2, 3, 7):
+        prm = pkg.default_params(nt=nt, compute_dtype=dmap[cd], state_dtype=dmap[sd], checkpoint_every=c)
+        with pkg.Handle(n, prm) as h:
+            grad, hv = h.new_vec(), h.new_vec()
+            e = h.lddmm_gradient(T(0.5 * vtrue), T(I0), T(I1), grad)
+            h.lddmm_hessvec(T(d), hv)
+            h.lddmm_hessvec(T(d), hv)  # twice: the resident segment moves between sweeps
+            h.lddmm_synchronize()
+            outs.append((e[0], grad.double().cpu().numpy(), hv.double().cpu().numpy(),
+                         pkg.workspace_bytes(n, prm)))
+    for e, gr, hvv, ws in outs[1:]:
+        assert abs(e - outs[0][0]) <= 1e-12 * abs(outs[0][0])
+        assert np.array_equal(gr, outs[0][1]) and np.array_equal(hvv, outs[0][2])
+    assert outs[1][3] < outs[0][3]
+
+
+def test_large_brain_shaped_grid_bf16_checkpointed(pkg):
+    """The 256 x 300 x 256 grid (FP32, bfloat16 states, checkpoint every 2
+    steps): one gradient and one Hv run and stay finite; the workspace is a
+    fraction of the fully stored FP32 one."""
+    n = (256, 300, 256)
+    prm = pkg.default_params(alpha=0.005, nt=10, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_BF16,
+                             checkpoint_every=2)
+    full = pkg.default_params(alpha=0.005, nt=10, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32)
+    assert pkg.workspace_bytes(n, prm) < 0.45 * pkg.workspace_bytes(n, full)
+    r = synth.rng_for(30)
+    P = synth.ellipsoid_phantom(n, r, perturb_vox=4.0)
+    v0 = synth.random_velocity(n, r, 8, 4.0)
+    f32 = torch.float32
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=f32, device="cuda")
+    with pkg.Handle(n, prm) as h:
+        grad, hv = h.new_vec(), h.new_vec()
+        e = h.lddmm_gradient(T(v0), T(P), T(np.roll(P, 2, axis=0)), grad)
+        h.lddmm_hessvec(grad, hv)
+        h.lddmm_synchronize()
+        assert np.isfinite(e).all()
+        assert torch.isfinite(grad).all() and torch.isfinite(hv).all()
+        assert float((grad * hv).sum()) > 0  # <g, H g> > 0: H is positive definite
