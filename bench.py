@@ -113,6 +113,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ----------------------------------------------------------------------------- replicas
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over the ranks of the default process group (x itself
+    without one).  Timings use it: the job's time is its slowest replica."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput of `world` independent replicas (units per second)."""
+    return world * units_per_rank / (ms_max / 1000.0)
+
+
 # ----------------------------------------------------------------------------- inputs
 def workload_inputs(n=N128, seed=1):
     """Phantom, true velocity and noise for the 128^3 workload (seeded)."""
@@ -341,12 +359,8 @@ def run_native(args, rank, world):
     torch.cuda.synchronize(dev)
     clocks = clk.stop()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1000.0)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
+    value = replica_throughput(args.steps, world, ms)
     hv_host = hv.double().cpu().numpy()
     finite = bool(np.isfinite(hv_host).all())
 
@@ -401,13 +415,8 @@ def e2e_run(args, h, d, hv, stream, dev, barrier, world, dist):
     ee1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
-    ems = ee0.elapsed_time(ee1)
-    if dist:
-        import torch.distributed as td
-        t = torch.tensor([ems], device=dev)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ems = float(t.item())
-    return world * args.steps / (ems / 1000.0)
+    ems = max_over_ranks(ee0.elapsed_time(ee1), dev)
+    return replica_throughput(args.steps, world, ems)
 
 
 def profile_run(h, delta, hv, value, world):
