@@ -39,6 +39,23 @@ struct SymD {
     int deriv;
     int mask;
 };
+// The same symbol with its scale already in the compute type, as the kernels
+// read it (a per-element double-to-float conversion would run on the slow
+// FP64 pipe).
+template <class T> struct SymT {
+    T scale;
+    int lpow;
+    int deriv;
+    int mask;
+};
+template <class T> inline SymT<T> to_symt(const SymD& s) {
+    SymT<T> r;
+    r.scale = (T)s.scale;
+    r.lpow = s.lpow;
+    r.deriv = s.deriv;
+    r.mask = s.mask;
+    return r;
+}
 
 // Per-axis symbol tables on the device (length n0, n1, n2/2+1).
 template <class T> struct SpecTabs {
@@ -51,13 +68,13 @@ template <class T> struct SpecTabs {
 };
 
 template <class T>
-__device__ __forceinline__ cpx<T> sym_apply(const SymD& sy, const SpecTabs<T>& tb, int k0, int k1, int k2, cpx<T> v) {
+__device__ __forceinline__ cpx<T> sym_apply(const SymT<T>& sy, const SpecTabs<T>& tb, int k0, int k1, int k2, cpx<T> v) {
     if (sy.mask) {
         const int a0 = k0 <= tb.n[0] / 2 ? k0 : tb.n[0] - k0;
         const int a1 = k1 <= tb.n[1] / 2 ? k1 : tb.n[1] - k1;
         if (a0 > tb.kcut[0] || a1 > tb.kcut[1] || k2 > tb.kcut[2]) return mk((T)0, (T)0);
     }
-    T f = (T)sy.scale;
+    T f = sy.scale;
     if (sy.lpow != 0) {
         T base = (T)1 + tb.alpha * (tb.ksq[0][k0] + tb.ksq[1][k1] + tb.ksq[2][k2]);
         int e = tb.s * (sy.lpow > 0 ? sy.lpow : -sy.lpow);
@@ -98,6 +115,36 @@ struct PassJob {
     double bcoef[MAXB];
     int nin, nout, nb, pad_;
 };
+// A job as the kernels read it: scalars in the compute type.
+template <class T> struct PassJobT {
+    const void* in[MAXI];
+    SymT<T> isym[MAXI];
+    void* out[MAXO];
+    SymT<T> osym[MAXO];
+    const void* base[MAXB];
+    T bcoef[MAXB];
+    int nin, nout, nb, pad_;
+};
+template <class T> inline PassJobT<T> to_jobt(const PassJob& j) {
+    PassJobT<T> r;
+    for (int i = 0; i < MAXI; ++i) {
+        r.in[i] = j.in[i];
+        r.isym[i] = to_symt<T>(j.isym[i]);
+    }
+    for (int i = 0; i < MAXO; ++i) {
+        r.out[i] = j.out[i];
+        r.osym[i] = to_symt<T>(j.osym[i]);
+    }
+    for (int i = 0; i < MAXB; ++i) {
+        r.base[i] = j.base[i];
+        r.bcoef[i] = (T)j.bcoef[i];
+    }
+    r.nin = j.nin;
+    r.nout = j.nout;
+    r.nb = j.nb;
+    r.pad_ = 0;
+    return r;
+}
 
 template <class T> struct PassParams {
     FFTAxis ax;
@@ -106,7 +153,7 @@ template <class T> struct PassParams {
     int sign;          // -1 forward, +1 inverse
     SpecTabs<T> tabs;
     int njobs;
-    PassJob jobs[MAXJOBS];
+    PassJobT<T> jobs[MAXJOBS];
 };
 
 }  // namespace lddmm

@@ -165,6 +165,19 @@ inline bool raise_smem_limit(K kernel, size_t need) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) == cudaSuccess;
 }
 
+// Grid of a persistent pass: three resident blocks per SM, never more blocks
+// than work items.
+inline int persistent_grid(int items) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    return std::max(1, std::min(items, 3 * sms));
+}
+
 // Launch of the register-blocked passes for the compiled line lengths.
 template <class T> struct FastPass {
     template <int N>
@@ -180,13 +193,13 @@ template <class T> struct FastPass {
         } else if (axis == 1) {
             const size_t sm = fast_c2c_smem<T, N>(1);
             if (set_attr) return raise_smem_limit(k_fast_c2c<T, N, 1>, sm);
-            const int gx = (int)(((size_t)n2h * n0 + TL - 1) / TL);
-            k_fast_c2c<T, N, 1><<<dim3(gx, nj), FAST_THREADS, sm, st>>>(pp);
+            const int ntiles = (int)(((size_t)n2h * n0 + TL - 1) / TL);
+            k_fast_c2c<T, N, 1><<<persistent_grid(ntiles * nj), FAST_THREADS, sm, st>>>(pp, ntiles);
         } else {
             const size_t sm = fast_c2c_smem<T, N>(0);
             if (set_attr) return raise_smem_limit(k_fast_c2c<T, N, 0>, sm);
-            const int gx = n2h * ((n1 + TL - 1) / TL);
-            k_fast_c2c<T, N, 0><<<dim3(gx, nj), FAST_THREADS, sm, st>>>(pp);
+            const int ntiles = n2h * ((n1 + TL - 1) / TL);
+            k_fast_c2c<T, N, 0><<<persistent_grid(ntiles * nj), FAST_THREADS, sm, st>>>(pp, ntiles);
         }
         return true;
     }
@@ -331,7 +344,7 @@ class Engine : public EngineBase {
         double b = 0;
         const double sc = (double)d.NS * sizeof(C), sr = (double)d.N * sizeof(T);
         for (int j = 0; j < q.njobs; ++j) {
-            const PassJob& jb = q.jobs[j];
+            const PassJobT<T>& jb = q.jobs[j];
             if (axis < 2) b += (jb.nin + jb.nb + jb.nout) * sc;
             else if (sign > 0) b += jb.nin * sc + jb.nout * sr;
             else b += jb.nin * sr + sc;
@@ -471,7 +484,9 @@ class Engine : public EngineBase {
             return fail(LDDMM_ERR_CUDA);
         for (int a = 0; a < 3; ++a) {
             PassParams<T> dummy;
-            fast[a] = FastPass<T>::has(ns[a]) && !force_generic_fft() &&
+            // 16-byte copies of axis-0 tile rows need an even n1 in FP32
+            const bool aligned = a != 0 || sizeof(T) == 8 || ns[1] % 2 == 0;
+            fast[a] = FastPass<T>::has(ns[a]) && aligned && !force_generic_fft() &&
                       FastPass<T>::launch(ns[a], a, 0, dummy, 0, 0, 0, 0, 0, st, true);
         }
         LD_CK(cudaDeviceSynchronize());
@@ -514,7 +529,7 @@ class Engine : public EngineBase {
             pp_.sign = sign;
             pp_.tabs = tabs;
             pp_.njobs = nj;
-            for (int j = 0; j < nj; ++j) pp_.jobs[j] = jobs[j0 + j];
+            for (int j = 0; j < nj; ++j) pp_.jobs[j] = to_jobt<T>(jobs[j0 + j]);
             if (fast[axis]) {
                 const int n = axis == 0 ? d.n0 : (axis == 1 ? d.n1 : d.n2);
                 PScope ps_(this, axis == 0 ? KC_AX0 : (axis == 1 ? KC_AX1 : KC_AX2), pass_bytes(axis, sign, pp_));
@@ -569,7 +584,7 @@ class Engine : public EngineBase {
             SpecComb<T> sc;
             sc.nin = 1;
             sc.in[0] = in + c * d.NS;
-            sc.sym[0] = sym(1.0, 0, -1, 1);
+            sc.sym[0] = to_symt<T>(sym(1.0, 0, -1, 1));
             {
                 PScope ps_(this, KC_SPEC, 2.0 * d.NS * sizeof(C));
                 k_spec_comb<T><<<pw_grid(d.NS), PW_THREADS, 0, st>>>(sc, tabs, d.n0, d.n1, d.n2h, out + c * d.NS);
@@ -1178,11 +1193,11 @@ class Engine : public EngineBase {
             sc.nin = 0;
             if (A) {
                 sc.in[sc.nin] = A + c * d.NS;
-                sc.sym[sc.nin++] = sa;
+                sc.sym[sc.nin++] = to_symt<T>(sa);
             }
             if (B) {
                 sc.in[sc.nin] = B + c * d.NS;
-                sc.sym[sc.nin++] = sb;
+                sc.sym[sc.nin++] = to_symt<T>(sb);
             }
             {
                 PScope ps_(this, KC_SPEC, (double)(sc.nin + 1) * d.NS * sizeof(C));

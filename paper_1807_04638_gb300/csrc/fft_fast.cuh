@@ -116,21 +116,46 @@ __device__ __forceinline__ void fast_fft(cpx<T> (&x)[FastPlan<N>::E], cpx<T>* b0
     fast_stages<T, N, E, N / E, FastPlan<N>::RADS, 0, 1, MAP>(x, b0, b1, c, t, tw, dir);
 }
 
+// ---------------------------------------------------------------- async copies
+// 16-byte asynchronous global -> shared copies (cp.async, completion by
+// commit / wait groups: no polling loop).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int P> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(P) : "memory");
+}
+
 // ---------------------------------------------------------------- C2C passes
-// AXIS 1: lines along k1 (contiguous), MAP 1: a warp covers 32/TPL lines.
-// AXIS 0: lines along k0 (stride n1), MAP 0: a warp covers TL columns.
+// Persistent blocks walk the (tile, job) work items of the launch; every
+// input tile of an item is a "load unit".  The next unit is copied into the
+// other half of a double-buffered shared-memory tile (cp.async) while the
+// current one is transformed, so DRAM latency overlaps the butterflies.
+//   AXIS 1: a tile is TL consecutive contiguous lines along k1 ([line][N]).
+//   AXIS 0: a tile is TL consecutive k1 columns of lines along k0 ([row][TL]).
+template <class T, int N, int AXIS> struct C2CGeom {
+    static constexpr int E = FastPlan<N>::E;
+    static constexpr int TPL = N / E;
+    static constexpr int TL = FAST_THREADS / TPL;
+    static constexpr int MAP = AXIS == 1 ? 1 : 0;
+    static constexpr int TILE = TL * N;  // complex elements of one staged tile
+};
+
 template <class T, int N, int AXIS>
-__global__ void __launch_bounds__(FAST_THREADS, FastOcc<T>::value) k_fast_c2c(const __grid_constant__ PassParams<T> pp) {
-    constexpr int E = FastPlan<N>::E;
-    constexpr int TPL = N / E;
-    constexpr int TL = FAST_THREADS / TPL;
-    constexpr int MAP = AXIS == 1 ? 1 : 0;
+__global__ void __launch_bounds__(FAST_THREADS, 3) k_fast_c2c(const __grid_constant__ PassParams<T> pp, int ntiles) {
+    using G = C2CGeom<T, N, AXIS>;
+    constexpr int E = G::E, TPL = G::TPL, TL = G::TL, MAP = G::MAP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T>* b0 = (cpx<T>*)smem_raw;
+    cpx<T>* stage[2];
+    stage[0] = (cpx<T>*)smem_raw;
+    stage[1] = stage[0] + G::TILE;
+    cpx<T>* b0 = stage[1] + G::TILE;
     cpx<T>* b1 = b0 + TL * SIdx<N, MAP>::LP;
-    const PassJob& job = pp.jobs[blockIdx.y];
     const cpx<T>* tw = (const cpx<T>*)pp.ax.tw;
     const int n0 = pp.n0, n1 = pp.n1, n2h = pp.n2h;
+    const int nitems = ntiles * pp.njobs;
     int c, t;
     if (MAP == 1) {
         c = threadIdx.x / TPL;
@@ -139,88 +164,141 @@ __global__ void __launch_bounds__(FAST_THREADS, FastOcc<T>::value) k_fast_c2c(co
         c = threadIdx.x % TL;
         t = threadIdx.x / TL;
     }
-    size_t gbase;
-    size_t gstride;
-    int k0b = 0, k1b = 0, k2b = 0;
-    bool valid;
-    if (AXIS == 1) {
-        const int line = blockIdx.x * TL + c;
-        valid = line < n2h * n0;
-        const int l = valid ? line : 0;
-        gbase = (size_t)l * n1;
-        gstride = 1;
-        k2b = l / n0;
-        k0b = l % n0;
-    } else {
-        const int tpk = (n1 + TL - 1) / TL;
-        const int k2t = blockIdx.x / tpk;
-        const int k1 = (blockIdx.x % tpk) * TL + c;
-        valid = k1 < n1;
-        gbase = (size_t)k2t * n0 * n1 + (valid ? k1 : 0);
-        gstride = n1;
-        k1b = valid ? k1 : 0;
-        k2b = k2t;
-    }
-    auto freq = [&](int p, int& k0, int& k1, int& k2) {
-        k0 = AXIS == 0 ? p : k0b;
-        k1 = AXIS == 1 ? p : k1b;
-        k2 = k2b;
+    const int tpk = (n1 + TL - 1) / TL;  // AXIS 0: tiles per k2 plane
+
+    // geometry of a tile: first global element, valid lines (columns)
+    auto tile_geo = [&](int tile, int& g0, int& nval, int& k2t, int& kb) {
+        if (AXIS == 1) {
+            const int line0 = tile * TL;
+            nval = min(TL, n2h * n0 - line0);
+            g0 = line0 * n1;
+            k2t = 0;
+            kb = line0;
+        } else {
+            k2t = tile / tpk;
+            kb = (tile % tpk) * TL;
+            nval = min(TL, n1 - kb);
+            g0 = k2t * n0 * n1 + kb;
+        }
     };
-    cpx<T> x[E];
-    if (pp.sign > 0) {
-        cpx<T> xin[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const size_t g = gbase + (size_t)(t + TPL * m) * gstride;
-            cpx<T> acc = mk((T)0, (T)0);
-            if (valid)
-                for (int b = 0; b < job.nin; ++b) acc = acc + (T)job.isym[b].scale * ((const cpx<T>*)job.in[b])[g];
-            xin[m] = acc;
+    // issue the copy of input q of item w into stage buffer sb
+    auto issue = [&](int w, int q, int sb) {
+        if (w < nitems) {
+            const PassJobT<T>& jb = pp.jobs[w / ntiles];
+            const cpx<T>* src = (const cpx<T>*)jb.in[q];
+            int g0, nval, k2t, kb;
+            tile_geo(w % ntiles, g0, nval, k2t, kb);
+            if (AXIS == 1) {
+                const int chunks = nval * N * (int)sizeof(cpx<T>) / 16;
+                for (int i = threadIdx.x; i < chunks; i += FAST_THREADS)
+                    cp_async16((char*)stage[sb] + 16 * i, (const char*)(src + g0) + 16 * i);
+            } else {
+                const int cpr = nval * (int)sizeof(cpx<T>) / 16;  // 16-byte chunks per row
+                for (int i = threadIdx.x; i < N * cpr; i += FAST_THREADS) {
+                    const int p = i / cpr, ch = i % cpr;
+                    cp_async16((char*)(stage[sb] + p * TL) + 16 * ch, (const char*)(src + g0 + p * n1) + 16 * ch);
+                }
+            }
         }
-        for (int o = 0; o < job.nout; ++o) {
-            const SymD sy = job.osym[o];
+        cp_async_commit();
+    };
+
+    // the unit sequence: items w = blockIdx.x, +gridDim.x, ...; inputs q = 0..nin-1
+    int w = blockIdx.x, q = 0, sb = 0;
+    int nw = w, nq = 0;  // the unit being prefetched
+    auto advance = [&](int& ww, int& qq) {
+        const PassJobT<T>& jb = pp.jobs[ww / ntiles];
+        if (++qq >= jb.nin) {
+            qq = 0;
+            ww += gridDim.x;
+        }
+    };
+    if (w < nitems) issue(nw, nq, 0);
+    advance(nw, nq);
+    cpx<T> x[E], acc[E];
+    while (w < nitems) {
+        // prefetch the next unit into the other buffer, then wait for this one
+        if (nw < nitems) issue(nw, nq, sb ^ 1);
+        else cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const int jw = w / ntiles;
+        const PassJobT<T>& job = pp.jobs[jw];
+        int g0, nval, k2t, kb;
+        tile_geo(w % ntiles, g0, nval, k2t, kb);
+        const bool valid = c < nval;
+        const cpx<T>* tile = stage[sb];
+        // frequency indices of the other two axes for this thread's line
+        int k0b, k1b, k2b;
+        if (AXIS == 1) {
+            const int line = kb + (valid ? c : 0);
+            k2b = line / n0;
+            k0b = line % n0;
+            k1b = 0;
+        } else {
+            k2b = k2t;
+            k1b = kb + (valid ? c : 0);
+            k0b = 0;
+        }
+        auto at = [&](int p) { return AXIS == 1 ? c * N + p : p * TL + c; };
+        auto gidx = [&](int p) { return AXIS == 1 ? g0 + c * n1 + p : g0 + p * n1 + c; };
+        const bool last = q == job.nin - 1;
+        if (pp.sign > 0) {
+            // inverse: lincomb of the inputs, then each output's symbol, IFFT, store
+            const T coef = job.isym[q].scale;
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                int k0, k1, k2;
-                freq(t + TPL * m, k0, k1, k2);
-                x[m] = sym_apply(sy, pp.tabs, k0, k1, k2, xin[m]);
+                const cpx<T> v = valid ? tile[at(t + TPL * m)] : mk((T)0, (T)0);
+                acc[m] = q == 0 ? coef * v : acc[m] + coef * v;
             }
-            fast_fft<T, N, MAP>(x, b0, b1, c, t, tw, +1);
-            if (valid) {
-                cpx<T>* out = (cpx<T>*)job.out[o];
+            __syncthreads();  // the stage buffer may now be refilled
+            if (last) {
+                for (int o = 0; o < job.nout; ++o) {
+                    const SymT<T> sy = job.osym[o];
 #pragma unroll
-                for (int m = 0; m < E; ++m) out[gbase + (size_t)(t + TPL * m) * gstride] = x[m];
+                    for (int m = 0; m < E; ++m) {
+                        const int p = t + TPL * m;
+                        x[m] = sym_apply(sy, pp.tabs, AXIS == 0 ? p : k0b, AXIS == 1 ? p : k1b, k2b, acc[m]);
+                    }
+                    fast_fft<T, N, MAP>(x, b0, b1, c, t, tw, +1);
+                    if (valid) {
+                        cpx<T>* out = (cpx<T>*)job.out[o];
+#pragma unroll
+                        for (int m = 0; m < E; ++m) out[gidx(t + TPL * m)] = x[m];
+                    }
+                }
             }
-        }
-    } else {
-        cpx<T> acc[E];
+        } else {
+            // forward: FFT of each input, post-symbol, accumulate; bases and store after the last
 #pragma unroll
-        for (int m = 0; m < E; ++m) acc[m] = mk((T)0, (T)0);
-        for (int q = 0; q < job.nin; ++q) {
-            const cpx<T>* in = (const cpx<T>*)job.in[q];
-#pragma unroll
-            for (int m = 0; m < E; ++m)
-                x[m] = valid ? in[gbase + (size_t)(t + TPL * m) * gstride] : mk((T)0, (T)0);
+            for (int m = 0; m < E; ++m) x[m] = valid ? tile[at(t + TPL * m)] : mk((T)0, (T)0);
+            __syncthreads();
             fast_fft<T, N, MAP>(x, b0, b1, c, t, tw, -1);
-            const SymD sy = job.isym[q];
+            const SymT<T> sy = job.isym[q];
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                int k0, k1, k2;
-                freq(t + TPL * m, k0, k1, k2);
-                acc[m] = acc[m] + sym_apply(sy, pp.tabs, k0, k1, k2, x[m]);
+                const int p = t + TPL * m;
+                const cpx<T> v = sym_apply(sy, pp.tabs, AXIS == 0 ? p : k0b, AXIS == 1 ? p : k1b, k2b, x[m]);
+                acc[m] = q == 0 ? v : acc[m] + v;
             }
-        }
-        if (valid) {
-            cpx<T>* out = (cpx<T>*)job.out[0];
+            if (last && valid) {
+                cpx<T>* out = (cpx<T>*)job.out[0];
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const size_t g = gbase + (size_t)(t + TPL * m) * gstride;
-                cpx<T> v = acc[m];
-                for (int b = 0; b < job.nb; ++b) v = v + (T)job.bcoef[b] * ((const cpx<T>*)job.base[b])[g];
-                out[g] = v;
+                for (int m = 0; m < E; ++m) {
+                    const int g = gidx(t + TPL * m);
+                    cpx<T> v = acc[m];
+                    for (int b = 0; b < job.nb; ++b) v = v + job.bcoef[b] * ((const cpx<T>*)job.base[b])[g];
+                    out[g] = v;
+                }
             }
         }
+        // next unit
+        w = nw;
+        q = nq;
+        if (nw < nitems) advance(nw, nq);
+        sb ^= 1;
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- axis-2 pass
@@ -238,7 +316,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FastOcc<T>::value) k_fast_axis2(
     cpx<T>* H = (cpx<T>*)smem_raw;
     cpx<T>* b0 = H + 2 * TL * PH;
     cpx<T>* b1 = b0 + TL * SIdx<N, 1>::LP;
-    const PassJob& job = pp.jobs[blockIdx.y];
+    const PassJobT<T>& job = pp.jobs[blockIdx.y];
     const cpx<T>* tw = (const cpx<T>*)pp.ax.tw;
     const int rows = pp.n0 * pp.n1;
     const int r0 = blockIdx.x * 2 * TL;
@@ -252,11 +330,11 @@ __global__ void __launch_bounds__(FAST_THREADS, FastOcc<T>::value) k_fast_axis2(
             cpx<T> acc = mk((T)0, (T)0);
             if (row < nr)
                 for (int b = 0; b < job.nin; ++b)
-                    acc = acc + (T)job.isym[b].scale * ((const cpx<T>*)job.in[b])[(size_t)k * rows + r0 + row];
+                    acc = acc + job.isym[b].scale * ((const cpx<T>*)job.in[b])[(size_t)k * rows + r0 + row];
             H[row * PH + k] = acc;
         }
         for (int o = 0; o < job.nout; ++o) {
-            const SymD sy = job.osym[o];
+            const SymT<T> sy = job.osym[o];
             __syncthreads();
 #pragma unroll
             for (int m = 0; m < E; ++m) {
@@ -300,7 +378,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FastOcc<T>::value) k_fast_axis2(
 #pragma unroll
             for (int m = 0; m < E; ++m) b0[SIdx<N, 1>::at(c, t + TPL * m)] = x[m];
             __syncthreads();
-            const SymD sy = job.isym[q];
+            const SymT<T> sy = job.isym[q];
             for (int k = t; k < NH; k += TPL) {
                 const cpx<T> zk = b0[SIdx<N, 1>::at(c, k)];
                 const cpx<T> zn = cj(b0[SIdx<N, 1>::at(c, k == 0 ? 0 : N - k)]);
@@ -322,7 +400,8 @@ __global__ void __launch_bounds__(FAST_THREADS, FastOcc<T>::value) k_fast_axis2(
 }
 
 template <class T, int N> constexpr size_t fast_c2c_smem(int axis) {
-    return (size_t)2 * (FAST_THREADS / (N / FastPlan<N>::E)) * (axis == 1 ? SIdx<N, 1>::LP : SIdx<N, 0>::LP) *
+    return ((size_t)2 * C2CGeom<T, N, 1>::TILE +
+            (size_t)2 * (FAST_THREADS / (N / FastPlan<N>::E)) * (axis == 1 ? SIdx<N, 1>::LP : SIdx<N, 0>::LP)) *
            sizeof(cpx<T>);
 }
 template <class T, int N> constexpr size_t fast_axis2_smem() {

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_pass_c2c(const __grid_constant_
     cpx<T>* X = (cpx<T>*)smem_raw;
     cpx<T>* A = X + TL * P;
     cpx<T>* B = A + TL * P;
-    const PassJob& job = pp.jobs[blockIdx.y];
+    const PassJobT<T>& job = pp.jobs[blockIdx.y];
     const int n0 = pp.n0, n1 = pp.n1, n2h = pp.n2h;
 
     int ncols, line0 = 0, k2t = 0, k10 = 0;
@@ -158,13 +158,13 @@ __global__ void __launch_bounds__(FFT_THREADS) k_pass_c2c(const __grid_constant_
             cpx<T> acc = mk((T)0, (T)0);
             for (int b = 0; b < job.nin; ++b) {
                 cpx<T> v = ((const cpx<T>*)job.in[b])[g];
-                acc = acc + (T)job.isym[b].scale * v;
+                acc = acc + job.isym[b].scale * v;
             }
             X[c * P + i] = acc;
         }
         __syncthreads();
         for (int o = 0; o < job.nout; ++o) {
-            const SymD sy = job.osym[o];
+            const SymT<T> sy = job.osym[o];
             for (int e = threadIdx.x; e < total; e += blockDim.x) {
                 int c, i, k0, k1, k2;
                 size_t g;
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_pass_c2c(const __grid_constant_
             }
             __syncthreads();
             cpx<T>* R = fft_tile(A, B, ncols, P, pp.ax, -1);
-            const SymD sy = job.isym[q];
+            const SymT<T> sy = job.isym[q];
             for (int e = threadIdx.x; e < total; e += blockDim.x) {
                 int c, i, k0, k1, k2;
                 size_t g;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_pass_c2c(const __grid_constant_
             size_t g;
             geo(e, c, i, g, k0, k1, k2);
             cpx<T> v = X[c * P + i];
-            for (int b = 0; b < job.nb; ++b) v = v + (T)job.bcoef[b] * ((const cpx<T>*)job.base[b])[g];
+            for (int b = 0; b < job.nb; ++b) v = v + job.bcoef[b] * ((const cpx<T>*)job.base[b])[g];
             out[g] = v;
         }
     }
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_pass_axis2(const __grid_constan
     cpx<T>* H = (cpx<T>*)smem_raw;
     cpx<T>* A = H + 2 * TL * Ph;
     cpx<T>* B = A + TL * P;
-    const PassJob& job = pp.jobs[blockIdx.y];
+    const PassJobT<T>& job = pp.jobs[blockIdx.y];
     const int r0 = blockIdx.x * 2 * TL;
     const int nr = min(2 * TL, rows - r0);
     const int npair = (nr + 1) / 2;
@@ -241,12 +241,12 @@ __global__ void __launch_bounds__(FFT_THREADS) k_pass_axis2(const __grid_constan
             cpx<T> acc = mk((T)0, (T)0);
             if (row < nr)
                 for (int b = 0; b < job.nin; ++b)
-                    acc = acc + (T)job.isym[b].scale * ((const cpx<T>*)job.in[b])[(size_t)k * rows + r0 + row];
+                    acc = acc + job.isym[b].scale * ((const cpx<T>*)job.in[b])[(size_t)k * rows + r0 + row];
             H[row * Ph + k] = acc;
         }
         __syncthreads();
         for (int o = 0; o < job.nout; ++o) {
-            const SymD sy = job.osym[o];
+            const SymT<T> sy = job.osym[o];
             for (int e = threadIdx.x; e < npair * n2; e += blockDim.x) {
                 const int c = e / n2, k = e % n2;
                 const bool lo = k < n2h;
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_pass_axis2(const __grid_constan
             }
             __syncthreads();
             cpx<T>* R = fft_tile(A, B, npair, P, pp.ax, -1);
-            const SymD sy = job.isym[q];
+            const SymT<T> sy = job.isym[q];
             for (int e = threadIdx.x; e < npair * n2h; e += blockDim.x) {
                 const int c = e / n2h, k = e % n2h;
                 const cpx<T> zk = R[c * P + k];

@@ -139,7 +139,8 @@ static lddmm_status noalloc_run(const Dims& d, double alpha, int s, int power, c
     bool fast[3];
     for (int a = 0; a < 3; ++a) {
         PassParams<T> dummy;
-        fast[a] = FastPass<T>::has(ns[a]) && !force_generic_fft() &&
+        const bool aligned = a != 0 || sizeof(T) == 8 || ns[1] % 2 == 0;
+        fast[a] = FastPass<T>::has(ns[a]) && aligned && !force_generic_fft() &&
                   FastPass<T>::launch(ns[a], a, 0, dummy, 0, 0, 0, 0, 0, st, true);
     }
     if (!raise_smem_limit(k_pass_c2c<T, 0>, smc[0]) || !raise_smem_limit(k_pass_c2c<T, 1>, smc[1]) ||
@@ -159,18 +160,19 @@ static lddmm_status noalloc_run(const Dims& d, double alpha, int s, int power, c
         pp.sign = sign;
         pp.tabs = tabs;
         pp.njobs = 1;
-        PassJob& j = pp.jobs[0];
+        PassJobT<T>& j = pp.jobs[0];
         j.nin = 1;
         j.in[0] = src;
         j.nout = 1;
         j.out[0] = dst;
-        SymD unit;
-        unit.scale = 1.0;
+        SymT<T> unit;
+        unit.scale = (T)1;
         unit.lpow = 0;
         unit.deriv = -1;
         unit.mask = 0;
-        j.isym[0] = sign > 0 ? unit : sy;
-        j.osym[0] = sign > 0 ? sy : unit;
+        const SymT<T> syt = to_symt<T>(sy);
+        j.isym[0] = sign > 0 ? unit : syt;
+        j.osym[0] = sign > 0 ? syt : unit;
         if (fast[axis]) {
             FastPass<T>::launch(ns[axis], axis, sign, pp, 1, d.rows, d.n0, d.n1, d.n2h, st);
         } else if (axis == 2) {

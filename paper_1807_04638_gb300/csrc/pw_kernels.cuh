@@ -394,7 +394,7 @@ __global__ void k_jacdet(const T* __restrict__ Du, T* __restrict__ J, size_t N) 
 // Spectral-space combination on [k2][k0][k1] arrays: out = sum_b sym_b . in_b
 template <class T> struct SpecComb {
     const cpx<T>* in[MAXI];
-    SymD sym[MAXI];
+    SymT<T> sym[MAXI];
     int nin;
 };
 template <class T>
