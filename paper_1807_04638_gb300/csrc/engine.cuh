@@ -211,10 +211,13 @@ template <class T> struct FastPass {
             case 64: return go<64>(axis, sign, pp, nj, rows, n0, n1, n2h, st, set_attr);
             case 128: return go<128>(axis, sign, pp, nj, rows, n0, n1, n2h, st, set_attr);
             case 256: return go<256>(axis, sign, pp, nj, rows, n0, n1, n2h, st, set_attr);
+            case 96: return go<96>(axis, sign, pp, nj, rows, n0, n1, n2h, st, set_attr);
+            case 160: return go<160>(axis, sign, pp, nj, rows, n0, n1, n2h, st, set_attr);
+            case 192: return go<192>(axis, sign, pp, nj, rows, n0, n1, n2h, st, set_attr);
             default: return false;
         }
     }
-    static bool has(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
+    static bool has(int n) { return n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 192 || n == 256; }
 };
 
 #define LD_CK(call)                                           \

@@ -21,12 +21,22 @@ template <> struct FastPlan<32> { static constexpr bool ok = true; static conste
 template <> struct FastPlan<64> { static constexpr bool ok = true; static constexpr int E = 8, RADS = 0x88; };
 template <> struct FastPlan<128> { static constexpr bool ok = true; static constexpr int E = 8, RADS = 0x448; };
 template <> struct FastPlan<256> { static constexpr bool ok = true; static constexpr int E = 8, RADS = 0x488; };
+// mixed radix: E is a multiple of every radix of the plan
+template <> struct FastPlan<96> { static constexpr bool ok = true; static constexpr int E = 12, RADS = 0x3244; };
+template <> struct FastPlan<192> { static constexpr bool ok = true; static constexpr int E = 12, RADS = 0x3444; };
+template <> struct FastPlan<160> { static constexpr bool ok = true; static constexpr int E = 20, RADS = 0x5244; };
 
 constexpr int FAST_THREADS = 256;
 // Resident blocks per SM the register budget is sized for: 4 for FP32
 // (<= 64 registers), 2 for FP64, so that enough loads are in flight to hide
 // DRAM latency.
-template <class T> struct FastOcc { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
+template <class T, int N> struct FastOcc {
+    static constexpr int value = FastPlan<N>::E > 12 ? 1 : (sizeof(T) == 4 ? (FastPlan<N>::E > 8 ? 3 : 4) : 2);
+};
+// resident blocks of the persistent C2C passes (double-buffered tiles)
+template <class T, int N> struct FastOccC2C {
+    static constexpr int value = FastPlan<N>::E > 12 ? 1 : (FastPlan<N>::E > 8 ? 2 : 3);
+};
 
 template <class T> struct Rad8 {
     // y_k = sum_r x_r w^{rk}, w = e^{dir 2 pi i / 8}
@@ -144,7 +154,7 @@ template <class T, int N, int AXIS> struct C2CGeom {
 };
 
 template <class T, int N, int AXIS>
-__global__ void __launch_bounds__(FAST_THREADS, 3) k_fast_c2c(const __grid_constant__ PassParams<T> pp, int ntiles) {
+__global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fast_c2c(const __grid_constant__ PassParams<T> pp, int ntiles) {
     using G = C2CGeom<T, N, AXIS>;
     constexpr int E = G::E, TPL = G::TPL, TL = G::TL, MAP = G::MAP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -306,7 +316,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fast_c2c(const __grid_const
 // spectrum of the block is staged in H[row][k] (pitch Ph) for the transposed
 // [k2][row] spectral layout.
 template <class T, int N>
-__global__ void __launch_bounds__(FAST_THREADS, FastOcc<T>::value) k_fast_axis2(const __grid_constant__ PassParams<T> pp) {
+__global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_axis2(const __grid_constant__ PassParams<T> pp) {
     constexpr int E = FastPlan<N>::E;
     constexpr int TPL = N / E;
     constexpr int TL = FAST_THREADS / TPL;

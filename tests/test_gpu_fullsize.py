@@ -140,3 +140,44 @@ def test_sweeps_and_hessian_properties_128(pkg, workload128):
     hxy, xhy = np.sum(host(hx) * Y), np.sum(X * host(hy))
     assert abs(hxy - xhy) < 1e-5 * (abs(hxy) + abs(xhy))
     assert np.sum(host(hx) * X) > 0 and np.isfinite(host(hx)).all()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n", [(96, 40, 32), (40, 96, 160), (192, 36, 48)])
+def test_mixed_radix_compiled_sizes(pkg, prec, n):
+    """Gradient and Hv on grids whose axes use the compiled 96/160/192 plans."""
+    dtype, cd = DT[prec]
+    nt = 2
+    g = O.Grid(n, alpha=0.01)
+    I0, vtrue = synth.blob_pair_inputs(n, 41, kmax=3, max_disp_vox=1.5)
+    I0 = synth.spectral_gaussian_smooth(I0, 1.0)
+    I1 = O.shoot(g, vtrue, nt, I0).m1
+    p = O.Params(nt=nt)
+    v0 = 0.5 * vtrue
+    gl2, E, _, _, tr = O.gradient(g, p, v0, I0, I1)
+    d = synth.band_limited_field(n, synth.rng_for(42), 6.0, 3) * g.h[0]
+    hl2 = O.hessvec(g, p, tr, d)
+    tol = 1e-10 if prec == "f64" else 1e-5
+    with pkg.Handle(n, pkg.default_params(nt=nt, compute_dtype=cd, state_dtype=cd)) as h:
+        grad, hv = h.new_vec(), h.new_vec()
+        e = h.lddmm_gradient(dev(v0, dtype), dev(I0, dtype), dev(I1, dtype), grad)
+        h.lddmm_hessvec(dev(d, dtype), hv)
+        h.lddmm_synchronize()
+    assert abs(e[0] - E) < tol * abs(E)
+    assert rel(host(grad), O.to_space(g, p, gl2)) < tol
+    assert rel(host(hv), O.to_space(g, p, hl2)) < tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_metric_160_192_96(pkg, prec):
+    dtype, cd = DT[prec]
+    n = (160, 192, 96)
+    g = O.Grid(n, alpha=0.005)
+    f = synth.rng_for(43).standard_normal((3,) + n)
+    tol = 1e-10 if prec == "f64" else 1e-5
+    with pkg.Handle(n, pkg.default_params(alpha=0.005, compute_dtype=cd, state_dtype=cd)) as h:
+        x = dev(f, dtype)
+        out = torch.empty_like(x)
+        h.lddmm_apply_metric(x, out, -1)
+        h.lddmm_synchronize()
+        assert rel(host(out), g.K(f)) < tol
