@@ -151,9 +151,19 @@ template <class T> struct PassParams {
     int n0, n1, n2, n2h;
     int TL, P, Ph;     // lines per tile, line pitch, half-spectrum pitch (axis-2 pass)
     int sign;          // -1 forward, +1 inverse
+    // Band of the transform (register-blocked passes): only the k2 planes
+    // k2 < nb2 and the k1 columns [0, c1) U [s1, n1) are transformed; every
+    // other spectral entry is treated as zero on input and left unwritten on
+    // output.  The full transform has nb2 = n2h, c1 = s1 = n1.
+    int nb2, c1, s1;
     SpecTabs<T> tabs;
     int njobs;
     PassJobT<T> jobs[MAXJOBS];
 };
+template <class T> inline void full_band(PassParams<T>& p) {
+    p.nb2 = p.n2h;
+    p.c1 = p.n1;
+    p.s1 = p.n1;
+}
 
 }  // namespace lddmm

@@ -5,7 +5,13 @@
 //       real_out = F^-1[ symbol . (sum_b c_b X_b) ]            (inverse)
 //       spec_out = sum_b c_b B_b + sum_i symbol_i . F(real_i)  (forward)
 //     into the three FFT passes (axis 0, axis 1, axis 2) with fan-out and
-//     combination inside each pass;
+//     combination inside each pass; with the 2/3-rule projector P on, the
+//     transforms of the shooting and of both Jacobi sweeps are band-limited:
+//     the passes touch only the k2 planes and k1 columns of the band (every
+//     source there is band-limited or read through P, every output is used
+//     through P only; the adjoint state's out-of-band part never reaches its
+//     band, since each operator of the transposed step maps out-of-band
+//     input to out-of-band output);
 //   * EPDiff shooting (Heun) with semi-Lagrangian map transport (Sec. 2.2,
 //     Sec. 3 of the paper), storing every stage's v, Dv, m = Lv, Dm;
 //   * the forward Jacobi (tangent) sweep and its exact transpose, the adjoint
@@ -127,6 +133,12 @@ inline bool force_generic_fft() {
     const char* e = getenv("LDDMM_GENERIC_FFT");
     return e && e[0] == '1';
 }
+// LDDMM_FULL_BAND=1 transforms every spectral line even where the 2/3-rule
+// band makes most of them zero; used to cross-check the band-limited passes.
+inline bool force_full_band() {
+    const char* e = getenv("LDDMM_FULL_BAND");
+    return e && e[0] == '1';
+}
 
 inline std::vector<int> radix_plan(int n) {
     std::vector<int> r;
@@ -193,12 +205,13 @@ template <class T> struct FastPass {
         } else if (axis == 1) {
             const size_t sm = fast_c2c_smem<T, N>(1);
             if (set_attr) return raise_smem_limit(k_fast_c2c<T, N, 1>, sm);
-            const int ntiles = (int)(((size_t)n2h * n0 + TL - 1) / TL);
+            (void)n2h;
+            const int ntiles = (int)(((size_t)pp.nb2 * n0 + TL - 1) / TL);
             k_fast_c2c<T, N, 1><<<persistent_grid(ntiles * nj), FAST_THREADS, sm, st>>>(pp, ntiles);
         } else {
             const size_t sm = fast_c2c_smem<T, N>(0);
             if (set_attr) return raise_smem_limit(k_fast_c2c<T, N, 0>, sm);
-            const int ntiles = n2h * ((n1 + TL - 1) / TL);
+            const int ntiles = pp.nb2 * ((pp.c1 + TL - 1) / TL + (n1 - pp.s1 + TL - 1) / TL);
             k_fast_c2c<T, N, 0><<<persistent_grid(ntiles * nj), FAST_THREADS, sm, st>>>(pp, ntiles);
         }
         return true;
@@ -273,6 +286,9 @@ class Engine : public EngineBase {
     SpecTabs<T> tabs;
     int TLc[2], Pc[2], TL2, P2, Ph2;
     bool fast[3] = {false, false, false};
+    // band-limited transforms (all three passes register-blocked, dealiasing on)
+    bool band_ok = false;
+    int bnb2 = 0, bc1 = 0, bs1 = 0;
     size_t smem_c[2], smem2;
     int pool_top = 0;
     bool lin_valid = false;
@@ -343,14 +359,18 @@ class Engine : public EngineBase {
         if (launches) *launches = acc_n[cls];
         return status;
     }
+    // Compulsory bytes of a pass: the spectral entries of the band it
+    // transforms (fp: planes, fc: k1 columns) and the real rows.
     double pass_bytes(int axis, int sign, const PassParams<T>& q) const {
         double b = 0;
         const double sc = (double)d.NS * sizeof(C), sr = (double)d.N * sizeof(T);
+        const double fp = (double)q.nb2 / d.n2h, fc = (double)(q.c1 + d.n1 - q.s1) / d.n1;
         for (int j = 0; j < q.njobs; ++j) {
             const PassJobT<T>& jb = q.jobs[j];
-            if (axis < 2) b += (jb.nin + jb.nb + jb.nout) * sc;
-            else if (sign > 0) b += jb.nin * sc + jb.nout * sr;
-            else b += jb.nin * sr + sc;
+            if (axis == 0) b += (jb.nin + jb.nb + jb.nout) * sc * fp * fc;
+            else if (axis == 1) b += (sign > 0 ? jb.nin * fc + jb.nout : jb.nin + jb.nout * fc) * sc * fp;
+            else if (sign > 0) b += jb.nin * sc * fp + jb.nout * sr;
+            else b += jb.nin * sr + sc * fp;
         }
         return b;
     }
@@ -424,7 +444,10 @@ class Engine : public EngineBase {
         pvt = carve<T>(3 * d.N);
         partial = carve<double>(RED_BLOCKS * 3);
         dres = carve<double>(NSLOT);
-        LD_CK(cudaMemset(base_, 0, off_));
+        // LDDMM_POISON_WORKSPACE=1 fills the buffers with NaN bytes instead of
+        // zeros, so that a test sees any read of an entry never written.
+        const char* poison = getenv("LDDMM_POISON_WORKSPACE");
+        LD_CK(cudaMemset(base_, poison && poison[0] == '1' ? 0xFF : 0, off_));
         // twiddles and symbol tables
         const int ns[3] = {d.n0, d.n1, d.n2};
         for (int a = 0; a < 3; ++a) {
@@ -492,6 +515,14 @@ class Engine : public EngineBase {
             fast[a] = FastPass<T>::has(ns[a]) && aligned && !force_generic_fft() &&
                       FastPass<T>::launch(ns[a], a, 0, dummy, 0, 0, 0, 0, 0, st, true);
         }
+        // the 2/3-rule band: k2 <= kcut2; k1 columns rounded outwards to even
+        // indices (16-byte copies of FP32 pairs)
+        bnb2 = std::min(tabs.kcut[2] + 1, d.n2h);
+        bc1 = (tabs.kcut[1] + 2) & ~1;
+        bs1 = (d.n1 - tabs.kcut[1]) & ~1;
+        if (bc1 >= bs1) bc1 = bs1 = d.n1;
+        band_ok = prm.dealias && fast[0] && fast[1] && fast[2] && !force_full_band() &&
+                  (bnb2 < d.n2h || bc1 < bs1);
         LD_CK(cudaDeviceSynchronize());
         return LDDMM_OK;
     }
@@ -520,7 +551,7 @@ class Engine : public EngineBase {
     double state_elem() const { return bf16 ? 2.0 : (double)sizeof(T); }
     double dt() const { return 1.0 / prm.nt; }
 
-    void launch(int axis, int sign, std::vector<PassJob>& jobs) {
+    void launch(int axis, int sign, std::vector<PassJob>& jobs, bool band) {
         for (size_t j0 = 0; j0 < jobs.size(); j0 += MAXJOBS) {
             const int nj = (int)std::min<size_t>(MAXJOBS, jobs.size() - j0);
             PassParams<T> pp_;
@@ -530,6 +561,12 @@ class Engine : public EngineBase {
             pp_.n2 = d.n2;
             pp_.n2h = d.n2h;
             pp_.sign = sign;
+            full_band(pp_);
+            if (band) {
+                pp_.nb2 = bnb2;
+                pp_.c1 = bc1;
+                pp_.s1 = bs1;
+            }
             pp_.tabs = tabs;
             pp_.njobs = nj;
             for (int j = 0; j < nj; ++j) pp_.jobs[j] = to_jobt<T>(jobs[j0 + j]);
@@ -611,7 +648,13 @@ class Engine : public EngineBase {
     }
 
     // real_out = F^-1[ sym . lincomb(src) ]
-    void inverse(const std::vector<SpecLin>& srcs, const std::vector<InvReq>& reqs) {
+    // band: every source is band-limited or every request is masked, so the
+    // transform may read the band only (the requests then all carry P).
+    void inverse(const std::vector<SpecLin>& srcs, const std::vector<InvReq>& reqs_in, bool band = false) {
+        const bool bd = band && band_ok;
+        std::vector<InvReq> reqs = reqs_in;
+        if (bd)
+            for (InvReq& q : reqs) q.sym.mask = 1;
         pool_top = 0;
         const double invN = 1.0 / (double)d.N;
         struct K0 {
@@ -683,7 +726,7 @@ class Engine : public EngineBase {
             }
             flush();
         }
-        launch(0, +1, jobs);
+        launch(0, +1, jobs, bd);
         // axis 1
         jobs.clear();
         for (size_t i0 = 0; i0 < k0s.size(); ++i0) {
@@ -699,7 +742,7 @@ class Engine : public EngineBase {
             }
             if (j.nout) jobs.push_back(j);
         }
-        launch(1, +1, jobs);
+        launch(1, +1, jobs, bd);
         // axis 2
         jobs.clear();
         for (size_t i1 = 0; i1 < k1s.size(); ++i1) {
@@ -723,11 +766,18 @@ class Engine : public EngineBase {
             }
             if (j.nout) jobs.push_back(j);
         }
-        launch(2, +1, jobs);
+        launch(2, +1, jobs, bd);
     }
 
     // spec_out = sum bases + sum_i sym_i . F(real_i)
-    void forward(const std::vector<FwdOut>& outs) {
+    // band: only the band of the output is ever used (it is masked, or every
+    // consumer applies P), so the transform writes the band only, with P.
+    void forward(const std::vector<FwdOut>& outs_in, bool band = false) {
+        const bool bd = band && band_ok;
+        std::vector<FwdOut> outs = outs_in;
+        if (bd)
+            for (FwdOut& o : outs)
+                for (FwdTerm& t : o.terms) t.sym.mask = 1;
         pool_top = 0;
         struct G {
             int o, lpow;
@@ -762,7 +812,7 @@ class Engine : public EngineBase {
                 g2[f].nin++;
             }
         }
-        launch(2, -1, j2);
+        launch(2, -1, j2, bd);
         // axis 1
         std::vector<G> g1;
         std::vector<PassJob> j1;
@@ -787,7 +837,7 @@ class Engine : public EngineBase {
             j.nin++;
             g1[f].nin++;
         }
-        launch(1, -1, j1);
+        launch(1, -1, j1, bd);
         // axis 0
         std::vector<PassJob> j0;
         for (size_t o = 0; o < outs.size(); ++o) {
@@ -815,7 +865,7 @@ class Engine : public EngineBase {
             }
             j0.push_back(j);
         }
-        launch(0, -1, j0);
+        launch(0, -1, j0, bd);
     }
 
     // comp c of a vector spectral lincomb
@@ -831,15 +881,15 @@ class Engine : public EngineBase {
     }
 
     // real vector field (3 comps) -> spectral
-    void fwd_vec(const T* in, C* out, double scale = 1.0, int lpow = 0) {
+    void fwd_vec(const T* in, C* out, double scale = 1.0, int lpow = 0, bool band = false) {
         std::vector<FwdOut> outs(3);
         for (int c = 0; c < 3; ++c) {
             outs[c].out = out + c * d.NS;
             outs[c].terms.push_back({in + c * d.N, sym(scale, lpow, -1)});
         }
-        forward(outs);
+        forward(outs, band);
     }
-    void inv_vec(const C* in, T* out, int ncomp = 3) {
+    void inv_vec(const C* in, T* out, int ncomp = 3, bool band = false) {
         std::vector<SpecLin> srcs;
         std::vector<InvReq> reqs;
         for (int c = 0; c < ncomp; ++c) {
@@ -850,10 +900,11 @@ class Engine : public EngineBase {
             srcs.push_back(s);
             reqs.push_back({c, sym(1.0, 0, -1), out + c * d.N});
         }
-        inverse(srcs, reqs);
+        inverse(srcs, reqs, band);
     }
 
-    // v, Dv, m = Lv, Dm of a spectral vector lincomb, into the 24-field layout
+    // v, Dv, m = Lv, Dm of a band-limited spectral vector lincomb, into the
+    // 24-field layout
     void eval_fields(std::initializer_list<std::pair<const C*, double>> terms, T* S, bool with_m = true) {
         std::vector<SpecLin> srcs;
         std::vector<InvReq> reqs;
@@ -866,7 +917,7 @@ class Engine : public EngineBase {
                 for (int j = 0; j < 3; ++j) reqs.push_back({c, sym(1.0, 1, j), S + (15 + 3 * c + j) * d.N});
             }
         }
-        inverse(srcs, reqs);
+        inverse(srcs, reqs, true);
     }
 
     // ------------------------------------------------------------ reductions
@@ -942,7 +993,7 @@ class Engine : public EngineBase {
                 outs[c].out = R1 + c * d.NS;
                 outs[c].terms.push_back({a + c * d.N, sym(-1.0, -1, -1, 1)});
             }
-            forward(outs);
+            forward(outs, true);
         }
         // stage 2 at v*_k = v_k + dt R1
         T* S2 = bf16 ? rs : state(2 * k + 1);
@@ -960,7 +1011,7 @@ class Engine : public EngineBase {
                 outs[c].bases.push_back({cur + c * d.NS, 1.0});
                 outs[c].bases.push_back({R1 + c * d.NS, 0.5 * dt_});
             }
-            forward(outs);
+            forward(outs, true);
         }
     }
 
@@ -1009,7 +1060,7 @@ class Engine : public EngineBase {
                 reqs.push_back({c, sym(1.0, 0, -1), vfin + c * d.N});
                 reqs.push_back({c, sym(1.0, 1, -1), vfin + (3 + c) * d.N});
             }
-            inverse(srcs, reqs);
+            inverse(srcs, reqs, true);
         }
         if (kinetic) dot_async(vfin + 3 * d.N, vfin, 3 * d.N, nt, d.cell);
         {
@@ -1075,7 +1126,7 @@ class Engine : public EngineBase {
                     reqs.push_back({3 + c, sym(1.0, 0, -1), X + c * d.N});
                     for (int j = 0; j < 3; ++j) reqs.push_back({3 + c, sym(1.0, 0, j), X + (3 + 3 * c + j) * d.N});
                 }
-                inverse(srcs, reqs);
+                inverse(srcs, reqs, true);
                 {
                     PScope ps_(this, KC_TANPW, 24.0 * d.N * state_elem() + 42.0 * d.N * sizeof(T));
                     if (bf16)
@@ -1108,7 +1159,7 @@ class Engine : public EngineBase {
                         ox.bases.push_back({be + c * d.NS, 0.5 * dt_ * dt_});
                     }
                 }
-                forward(outs);
+                forward(outs, true);
             }
         }
     }
@@ -1143,7 +1194,7 @@ class Engine : public EngineBase {
                     reqs.push_back({c, sym(1.0, -1, -1, 1), Y + c * d.N});
                     reqs.push_back({3 + c, sym(1.0, 0, -1, 1), Y + (3 + c) * d.N});
                 }
-                inverse(srcs, reqs);
+                inverse(srcs, reqs, true);
                 {
                     PScope ps_(this, KC_ADJPW, 24.0 * d.N * state_elem() + 42.0 * d.N * sizeof(T));
                     if (bf16)
@@ -1182,7 +1233,7 @@ class Engine : public EngineBase {
                         ox.bases.push_back({axp + c * d.NS, 0.5 * dt_});
                     }
                 }
-                forward(outs);
+                forward(outs, true);
             }
             cur_i = 1 - cur_i;
         }
@@ -1224,7 +1275,7 @@ class Engine : public EngineBase {
             PScope ps_(this, KC_MISC, 8.0 * d.N * sizeof(T));
             k_final_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, gm1, nullptr, rs, 0, d.N);
         }
-        fwd_vec(rs, adj[0] + 3 * d.NS);
+        fwd_vec(rs, adj[0] + 3 * d.NS, 1.0, 0, true);
         cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
         adjoint_sweep();
         // g_L2 = 2 w L v0 + T^T b ;  V: K g_L2 = 2 w v0 + K T^T b
@@ -1241,13 +1292,13 @@ class Engine : public EngineBase {
         cudaMemsetAsync(tan_[0] + 3 * d.NS, 0, 3 * d.NS * sizeof(C), st);
         tangent_sweep();
         T* xi = rs;
-        inv_vec(tan_[prm.nt % 2] + 3 * d.NS, xi);
+        inv_vec(tan_[prm.nt % 2] + 3 * d.NS, xi, 3, true);
         T* c = rs + 3 * d.N;
         {
             PScope ps_(this, KC_MISC, 8.0 * d.N * sizeof(T));
             k_final_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, nullptr, gm1, xi, c, 1, d.N);
         }
-        fwd_vec(c, adj[0] + 3 * d.NS);
+        fwd_vec(c, adj[0] + 3 * d.NS, 1.0, 0, true);
         cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
         adjoint_sweep();
         const double w2 = 2.0 * prm.weight;
@@ -1310,8 +1361,8 @@ class Engine : public EngineBase {
         mask_copy(dhat, tan_[0]);
         cudaMemsetAsync(tan_[0] + 3 * d.NS, 0, 3 * d.NS * sizeof(C), st);
         tangent_sweep();
-        if (eta1) inv_vec(tan_[prm.nt % 2], (T*)eta1);
-        if (xi1) inv_vec(tan_[prm.nt % 2] + 3 * d.NS, (T*)xi1);
+        if (eta1) inv_vec(tan_[prm.nt % 2], (T*)eta1, 3, true);
+        if (xi1) inv_vec(tan_[prm.nt % 2] + 3 * d.NS, (T*)xi1, 3, true);
         return check_launch();
     }
 
@@ -1319,8 +1370,8 @@ class Engine : public EngineBase {
         if (status != LDDMM_OK) return status;
         if (!bxi || !out) return fail(LDDMM_ERR_ARG);
         if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
-        fwd_vec((const T*)bxi, adj[0] + 3 * d.NS);
-        if (beta) fwd_vec((const T*)beta, adj[0]);
+        fwd_vec((const T*)bxi, adj[0] + 3 * d.NS, 1.0, 0, true);
+        if (beta) fwd_vec((const T*)beta, adj[0], 1.0, 0, true);
         else cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
         adjoint_sweep();
         spec_to_real2(nullptr, sym(0.0, 0, -1), adj_result(), sym(1.0, 0, -1, 1), (T*)out);
@@ -1386,7 +1437,7 @@ class Engine : public EngineBase {
             PScope ps_(this, KC_MISC, 8.0 * d.N * sizeof(T));
             k_vjp_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>((const T*)G, gm1, rs, d.N);
         }
-        fwd_vec(rs, adj[0] + 3 * d.NS);
+        fwd_vec(rs, adj[0] + 3 * d.NS, 1.0, 0, true);
         cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
         adjoint_sweep();
         spec_to_real2(nullptr, sym(0.0, 0, -1), adj_result(), sym(1.0, 0, -1, 1), (T*)out);

@@ -9,6 +9,15 @@
 // exchange).  The final stage leaves element t + TPL*m in register m, which
 // is stored straight to global memory.  Same jobs and layouts as the generic
 // passes in fft_kernels.cuh.
+//
+// Band-limited transforms (PassParams::nb2, c1, s1): under the 2/3-rule
+// projector P most of the half spectrum is zero or never used, so a pass can
+// be restricted to the k2 planes and k1 columns of the band.  The axis-2 pass
+// reads (inverse) or writes (forward) only the planes k2 < nb2; the axis-1
+// pass transforms only the lines of those planes and reads (inverse) or
+// writes (forward) only the band's k1 entries; the axis-0 pass transforms
+// only the lines (k2, k1) inside the band.  Skipped inputs count as zero and
+// skipped outputs are left unwritten.
 #pragma once
 #include "common.cuh"
 #include "fft_kernels.cuh"
@@ -174,23 +183,35 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
         c = threadIdx.x % TL;
         t = threadIdx.x / TL;
     }
-    const int tpk = (n1 + TL - 1) / TL;  // AXIS 0: tiles per k2 plane
+    // band: k2 planes < nb2; k1 columns [0, c1) and [s1, n1)
+    const int nb2 = pp.nb2, c1 = pp.c1, s1 = pp.s1;
+    const int tA = (c1 + TL - 1) / TL;                // AXIS 0: tiles of the first column range
+    const int tpk = tA + (n1 - s1 + TL - 1) / TL;      // AXIS 0: tiles per k2 plane
+    (void)n2h;
 
     // geometry of a tile: first global element, valid lines (columns)
     auto tile_geo = [&](int tile, int& g0, int& nval, int& k2t, int& kb) {
         if (AXIS == 1) {
             const int line0 = tile * TL;
-            nval = min(TL, n2h * n0 - line0);
+            nval = min(TL, nb2 * n0 - line0);
             g0 = line0 * n1;
             k2t = 0;
             kb = line0;
         } else {
             k2t = tile / tpk;
-            kb = (tile % tpk) * TL;
-            nval = min(TL, n1 - kb);
+            const int r = tile % tpk;
+            if (r < tA) {
+                kb = r * TL;
+                nval = min(TL, c1 - kb);
+            } else {
+                kb = s1 + (r - tA) * TL;
+                nval = min(TL, n1 - kb);
+            }
             g0 = k2t * n0 * n1 + kb;
         }
     };
+    // AXIS 1 inverse: spectral entries k1 in [c1, s1) are zero (not read)
+    auto k1_out = [&](int p) { return AXIS == 1 && p >= c1 && p < s1; };
     // issue the copy of input q of item w into stage buffer sb
     auto issue = [&](int w, int q, int sb) {
         if (w < nitems) {
@@ -200,8 +221,12 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
             tile_geo(w % ntiles, g0, nval, k2t, kb);
             if (AXIS == 1) {
                 const int chunks = nval * N * (int)sizeof(cpx<T>) / 16;
-                for (int i = threadIdx.x; i < chunks; i += FAST_THREADS)
+                const bool skip = pp.sign > 0 && c1 < s1;
+                for (int i = threadIdx.x; i < chunks; i += FAST_THREADS) {
+                    // c1, s1 are even: a 16-byte chunk lies wholly inside or outside the band
+                    if (skip && k1_out((16 * i / (int)sizeof(cpx<T>)) % N)) continue;
                     cp_async16((char*)stage[sb] + 16 * i, (const char*)(src + g0) + 16 * i);
+                }
             } else {
                 const int cpr = nval * (int)sizeof(cpx<T>) / 16;  // 16-byte chunks per row
                 for (int i = threadIdx.x; i < N * cpr; i += FAST_THREADS) {
@@ -258,7 +283,8 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
             const T coef = job.isym[q].scale;
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                const cpx<T> v = valid ? tile[at(t + TPL * m)] : mk((T)0, (T)0);
+                const int p = t + TPL * m;
+                const cpx<T> v = valid && !k1_out(p) ? tile[at(p)] : mk((T)0, (T)0);
                 acc[m] = q == 0 ? coef * v : acc[m] + coef * v;
             }
             __syncthreads();  // the stage buffer may now be refilled
@@ -295,6 +321,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
                 cpx<T>* out = (cpx<T>*)job.out[0];
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
+                    if (k1_out(t + TPL * m)) continue;  // outside the band: not written
                     const int g = gidx(t + TPL * m);
                     cpx<T> v = acc[m];
                     for (int b = 0; b < job.nb; ++b) v = v + job.bcoef[b] * ((const cpx<T>*)job.base[b])[g];
@@ -338,7 +365,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
         for (int e = threadIdx.x; e < 2 * TL * NH; e += FAST_THREADS) {
             const int row = e % (2 * TL), k = e / (2 * TL);
             cpx<T> acc = mk((T)0, (T)0);
-            if (row < nr)
+            if (row < nr && k < pp.nb2)
                 for (int b = 0; b < job.nin; ++b)
                     acc = acc + job.isym[b].scale * ((const cpx<T>*)job.in[b])[(size_t)k * rows + r0 + row];
             H[row * PH + k] = acc;
@@ -389,7 +416,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
             for (int m = 0; m < E; ++m) b0[SIdx<N, 1>::at(c, t + TPL * m)] = x[m];
             __syncthreads();
             const SymT<T> sy = job.isym[q];
-            for (int k = t; k < NH; k += TPL) {
+            for (int k = t; k < pp.nb2; k += TPL) {
                 const cpx<T> zk = b0[SIdx<N, 1>::at(c, k)];
                 const cpx<T> zn = cj(b0[SIdx<N, 1>::at(c, k == 0 ? 0 : N - k)]);
                 const cpx<T> sa = sym_apply(sy, pp.tabs, 0, 0, k, (T)0.5 * (zk + zn));
@@ -402,7 +429,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
         }
         __syncthreads();
         cpx<T>* out = (cpx<T>*)job.out[0];
-        for (int e = threadIdx.x; e < 2 * TL * NH; e += FAST_THREADS) {
+        for (int e = threadIdx.x; e < 2 * TL * pp.nb2; e += FAST_THREADS) {
             const int row = e % (2 * TL), k = e / (2 * TL);
             if (row < nr) out[(size_t)k * rows + r0 + row] = H[row * PH + k];
         }

@@ -158,6 +158,7 @@ static lddmm_status noalloc_run(const Dims& d, double alpha, int s, int power, c
         pp.n2 = d.n2;
         pp.n2h = d.n2h;
         pp.sign = sign;
+        full_band(pp);
         pp.tabs = tabs;
         pp.njobs = 1;
         PassJobT<T>& j = pp.jobs[0];

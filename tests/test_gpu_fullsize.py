@@ -181,3 +181,82 @@ def test_metric_160_192_96(pkg, prec):
         h.lddmm_apply_metric(x, out, -1)
         h.lddmm_synchronize()
         assert rel(host(out), g.K(f)) < tol
+
+
+def test_band_limited_passes_equal_full_transforms(pkg, workload128, monkeypatch):
+    """With the 2/3-rule projector the shooting and Jacobi-sweep transforms
+    touch only the band; the results equal those of full transforms (the
+    skipped entries are zero or only ever used through P)."""
+    P, v0t, e0, e1, d = workload128
+    n = (128, 128, 128)
+    f32 = torch.float32
+    prm = pkg.default_params(alpha=0.005, nt=10, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32)
+    out = {}
+    for mode in ("band", "full"):
+        if mode == "full":
+            monkeypatch.setenv("LDDMM_FULL_BAND", "1")
+        else:
+            monkeypatch.delenv("LDDMM_FULL_BAND", raising=False)
+        monkeypatch.setenv("LDDMM_POISON_WORKSPACE", "1")
+        with pkg.Handle(n, prm) as h:
+            grad, hv, xi1, a0 = h.new_vec(), h.new_vec(), h.new_vec(), h.new_vec()
+            e = h.lddmm_gradient(dev(0.5 * v0t, f32), dev(P + e0, f32), dev(P + e1, f32), grad)
+            h.lddmm_hessvec(dev(d, f32), hv)
+            h.lddmm_jacobi_forward(dev(d, f32), None, xi1)
+            h.lddmm_jacobi_adjoint(None, dev(d, f32), a0)
+            h.lddmm_synchronize()
+            out[mode] = (e, host(grad), host(hv), host(xi1), host(a0))
+    eb, ef = out["band"][0], out["full"][0]
+    assert np.allclose(eb, ef, rtol=1e-12, atol=0)
+    for a, b in zip(out["band"][1:], out["full"][1:]):
+        assert np.isfinite(a).all()
+        assert rel(a, b) < 1e-6, rel(a, b)
+
+
+_BAND_CASES = {}
+
+
+def _band_case(n):
+    """Oracle results for the band-limited grid tests (computed once per grid)."""
+    if n not in _BAND_CASES:
+        nt = 3
+        g = O.Grid(n, alpha=0.01)
+        I0, vtrue = synth.blob_pair_inputs(n, 51, kmax=3, max_disp_vox=1.5)
+        I0 = synth.spectral_gaussian_smooth(I0, 1.0)
+        I1 = O.shoot(g, vtrue, nt, I0).m1
+        p = O.Params(nt=nt)
+        v0 = 0.5 * vtrue
+        gl2, E, _, _, tr = O.gradient(g, p, v0, I0, I1)
+        r = synth.rng_for(52)
+        dvec = synth.band_limited_field(n, r, 6.0, 3) * g.h[0]
+        be, bx = r.standard_normal((3,) + n), r.standard_normal((3,) + n)
+        want = dict(E=E, grad=O.to_space(g, p, gl2), hv=O.to_space(g, p, O.hessvec(g, p, tr, dvec)),
+                    tan=O.tangent(g, tr, dvec), adj=O.adjoint(g, tr, bx, be))
+        _BAND_CASES[n] = (nt, I0, I1, v0, dvec, be, bx, want)
+    return _BAND_CASES[n]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n", [(32, 64, 96), (96, 32, 64)])
+def test_band_limited_grids_vs_oracle(pkg, prec, n, monkeypatch):
+    """Grids whose three axes all use compiled plans (band-limited passes),
+    with a NaN-poisoned workspace: gradient, Hv and both sweeps against the
+    oracle."""
+    monkeypatch.setenv("LDDMM_POISON_WORKSPACE", "1")
+    monkeypatch.delenv("LDDMM_FULL_BAND", raising=False)
+    dtype, cd = DT[prec]
+    nt, I0, I1, v0, dvec, be, bx, want = _band_case(n)
+    tol = 1e-10 if prec == "f64" else 1e-5
+    with pkg.Handle(n, pkg.default_params(nt=nt, compute_dtype=cd, state_dtype=cd)) as h:
+        grad, hv, e1g, x1g, a0g = (h.new_vec() for _ in range(5))
+        e = h.lddmm_gradient(dev(v0, dtype), dev(I0, dtype), dev(I1, dtype), grad)
+        h.lddmm_hessvec(dev(dvec, dtype), hv)
+        h.lddmm_jacobi_forward(dev(dvec, dtype), e1g, x1g)
+        h.lddmm_jacobi_adjoint(dev(be, dtype), dev(bx, dtype), a0g)
+        h.lddmm_synchronize()
+    assert abs(e[0] - want["E"]) < tol * abs(want["E"])
+    assert rel(host(grad), want["grad"]) < tol
+    assert rel(host(hv), want["hv"]) < tol
+    assert rel(host(e1g), want["tan"][0]) < tol
+    assert rel(host(x1g), want["tan"][1]) < tol
+    assert rel(host(a0g), want["adj"]) < tol
