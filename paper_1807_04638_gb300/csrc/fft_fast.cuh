@@ -79,12 +79,19 @@ __device__ __forceinline__ void dft_r(cpx<T>* v, int dir) {
     else Rad<T>::r5(v, dir);
 }
 
-// Shared-memory index of element p of line c.
-//  MAP 1 (t fastest in a warp): one pad slot every 8 elements inside a line.
-//  MAP 0 (c fastest in a warp): odd line pitch.
-template <int N, int MAP> struct SIdx {
-    static constexpr int LP = MAP == 1 ? N + N / 8 + 1 : N + 1;
-    static __device__ __forceinline__ int at(int c, int p) { return MAP == 1 ? c * LP + p + (p >> 3) : c * LP + p; }
+// Shared-memory index of element p of line c.  The layouts keep every
+// exchange of every Stockham stage and every line read free of bank conflicts
+// (checked against a model of the 32 four-byte banks for all compiled plans,
+// FP32 and FP64):
+//  MAP 1 (t fastest in a warp): one pad slot every 8 (N = 128, 256: 16)
+//        elements inside a line, no pad between lines.
+//  MAP 0 (c fastest in a warp): odd line pitch (FP32, N = 256: one pad slot
+//        every 16 elements and two between lines).
+template <class T, int N, int MAP> struct SIdx {
+    static constexpr int SH = MAP == 1 ? ((N == 128 || N == 256) ? 4 : 3) : 4;
+    static constexpr bool PADDED = MAP == 1 || (sizeof(T) == 4 && N == 256);
+    static constexpr int LP = PADDED ? N + (N >> SH) + (MAP == 1 ? 0 : 2) : N + 1;
+    static __device__ __forceinline__ int at(int c, int p) { return PADDED ? c * LP + p + (p >> SH) : c * LP + p; }
 };
 
 template <class T, int N, int E, int TPL, int RADS, int S, int NS, int MAP>
@@ -116,13 +123,13 @@ __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* 
         } else {
             const int base = (j / NS) * NS * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) b0[SIdx<N, MAP>::at(c, base + r * NS)] = v[r];
+            for (int r = 0; r < R; ++r) b0[SIdx<T, N, MAP>::at(c, base + r * NS)] = v[r];
         }
     }
     if constexpr (!LAST) {
         __syncthreads();
 #pragma unroll
-        for (int m = 0; m < E; ++m) x[m] = b0[SIdx<N, MAP>::at(c, t + TPL * m)];
+        for (int m = 0; m < E; ++m) x[m] = b0[SIdx<T, N, MAP>::at(c, t + TPL * m)];
         fast_stages<T, N, E, TPL, RADS, S + 1, NS * R, MAP>(x, b1, b0, c, t, tw, dir);
     }
 }
@@ -167,11 +174,11 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
     using G = C2CGeom<T, N, AXIS>;
     constexpr int E = G::E, TPL = G::TPL, TL = G::TL, MAP = G::MAP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T>* stage[2];
-    stage[0] = (cpx<T>*)smem_raw;
-    stage[1] = stage[0] + G::TILE;
-    cpx<T>* b0 = stage[1] + G::TILE;
-    cpx<T>* b1 = b0 + TL * SIdx<N, MAP>::LP;
+    // the two stage buffers: stage0 + sb * TILE (pointer arithmetic, not an
+    // indexed array, which would live in local memory)
+    cpx<T>* const stage0 = (cpx<T>*)smem_raw;
+    cpx<T>* b0 = stage0 + 2 * G::TILE;
+    cpx<T>* b1 = b0 + TL * SIdx<T, N, MAP>::LP;
     const cpx<T>* tw = (const cpx<T>*)pp.ax.tw;
     const int n0 = pp.n0, n1 = pp.n1, n2h = pp.n2h;
     const int nitems = ntiles * pp.njobs;
@@ -225,13 +232,13 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
                 for (int i = threadIdx.x; i < chunks; i += FAST_THREADS) {
                     // c1, s1 are even: a 16-byte chunk lies wholly inside or outside the band
                     if (skip && k1_out((16 * i / (int)sizeof(cpx<T>)) % N)) continue;
-                    cp_async16((char*)stage[sb] + 16 * i, (const char*)(src + g0) + 16 * i);
+                    cp_async16((char*)(stage0 + sb * G::TILE) + 16 * i, (const char*)(src + g0) + 16 * i);
                 }
             } else {
                 const int cpr = nval * (int)sizeof(cpx<T>) / 16;  // 16-byte chunks per row
                 for (int i = threadIdx.x; i < N * cpr; i += FAST_THREADS) {
                     const int p = i / cpr, ch = i % cpr;
-                    cp_async16((char*)(stage[sb] + p * TL) + 16 * ch, (const char*)(src + g0 + p * n1) + 16 * ch);
+                    cp_async16((char*)((stage0 + sb * G::TILE) + p * TL) + 16 * ch, (const char*)(src + g0 + p * n1) + 16 * ch);
                 }
             }
         }
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
         int g0, nval, k2t, kb;
         tile_geo(w % ntiles, g0, nval, k2t, kb);
         const bool valid = c < nval;
-        const cpx<T>* tile = stage[sb];
+        const cpx<T>* tile = (stage0 + sb * G::TILE);
         // frequency indices of the other two axes for this thread's line
         int k0b, k1b, k2b;
         if (AXIS == 1) {
@@ -352,7 +359,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* H = (cpx<T>*)smem_raw;
     cpx<T>* b0 = H + 2 * TL * PH;
-    cpx<T>* b1 = b0 + TL * SIdx<N, 1>::LP;
+    cpx<T>* b1 = b0 + TL * SIdx<T, N, 1>::LP;
     const PassJobT<T>& job = pp.jobs[blockIdx.y];
     const cpx<T>* tw = (const cpx<T>*)pp.ax.tw;
     const int rows = pp.n0 * pp.n1;
@@ -413,12 +420,12 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
             // stage the packed spectrum to pair Z_k with Z_{N-k}
             __syncthreads();
 #pragma unroll
-            for (int m = 0; m < E; ++m) b0[SIdx<N, 1>::at(c, t + TPL * m)] = x[m];
+            for (int m = 0; m < E; ++m) b0[SIdx<T, N, 1>::at(c, t + TPL * m)] = x[m];
             __syncthreads();
             const SymT<T> sy = job.isym[q];
             for (int k = t; k < pp.nb2; k += TPL) {
-                const cpx<T> zk = b0[SIdx<N, 1>::at(c, k)];
-                const cpx<T> zn = cj(b0[SIdx<N, 1>::at(c, k == 0 ? 0 : N - k)]);
+                const cpx<T> zk = b0[SIdx<T, N, 1>::at(c, k)];
+                const cpx<T> zn = cj(b0[SIdx<T, N, 1>::at(c, k == 0 ? 0 : N - k)]);
                 const cpx<T> sa = sym_apply(sy, pp.tabs, 0, 0, k, (T)0.5 * (zk + zn));
                 const cpx<T> sb = sym_apply(sy, pp.tabs, 0, 0, k, rot((T)0.5 * (zk - zn), -1));
                 cpx<T>* ha = &H[(2 * c) * PH + k];
@@ -438,14 +445,14 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
 
 template <class T, int N> constexpr size_t fast_c2c_smem(int axis) {
     return ((size_t)2 * C2CGeom<T, N, 1>::TILE +
-            (size_t)2 * (FAST_THREADS / (N / FastPlan<N>::E)) * (axis == 1 ? SIdx<N, 1>::LP : SIdx<N, 0>::LP)) *
+            (size_t)2 * (FAST_THREADS / (N / FastPlan<N>::E)) * (axis == 1 ? SIdx<T, N, 1>::LP : SIdx<T, N, 0>::LP)) *
            sizeof(cpx<T>);
 }
 template <class T, int N> constexpr size_t fast_axis2_smem() {
     constexpr int TL = FAST_THREADS / (N / FastPlan<N>::E);
     constexpr int NH = N / 2 + 1;
     constexpr int PH = (NH % 2 == 0) ? NH + 1 : NH;
-    return ((size_t)2 * TL * PH + (size_t)2 * TL * SIdx<N, 1>::LP) * sizeof(cpx<T>);
+    return ((size_t)2 * TL * PH + (size_t)2 * TL * SIdx<T, N, 1>::LP) * sizeof(cpx<T>);
 }
 
 }  // namespace lddmm
