@@ -67,6 +67,12 @@ template <class T> struct SpecTabs {
     int kcut[3];  // band of the dealiasing projector P (n when dealiasing is off)
 };
 
+// a / b for the symbols: the fast-division intrinsic in FP32 (at most two
+// ulp for the positive, moderate L_hat^|lpow| values here), exact division in
+// FP64
+__device__ __forceinline__ float sym_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sym_div(double a, double b) { return a / b; }
+
 template <class T>
 __device__ __forceinline__ cpx<T> sym_apply(const SymT<T>& sy, const SpecTabs<T>& tb, int k0, int k1, int k2, cpx<T> v) {
     if (sy.mask) {
@@ -80,7 +86,7 @@ __device__ __forceinline__ cpx<T> sym_apply(const SymT<T>& sy, const SpecTabs<T>
         int e = tb.s * (sy.lpow > 0 ? sy.lpow : -sy.lpow);
         T p = (T)1;
         for (int q = 0; q < e; ++q) p *= base;
-        f = sy.lpow > 0 ? f * p : f / p;
+        f = sy.lpow > 0 ? f * p : sym_div(f, p);
     }
     if (sy.deriv >= 0) {
         int kk = sy.deriv == 0 ? k0 : (sy.deriv == 1 ? k1 : k2);

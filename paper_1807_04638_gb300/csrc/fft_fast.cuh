@@ -79,19 +79,41 @@ __device__ __forceinline__ void dft_r(cpx<T>* v, int dir) {
     else Rad<T>::r5(v, dir);
 }
 
-// Shared-memory index of element p of line c.  The layouts keep every
-// exchange of every Stockham stage and every line read free of bank conflicts
-// (checked against a model of the 32 four-byte banks for all compiled plans,
-// FP32 and FP64):
-//  MAP 1 (t fastest in a warp): one pad slot every 8 (N = 128, 256: 16)
-//        elements inside a line, no pad between lines.
+// Shared-memory index of element p of line c.  A half-warp's 8-byte (FP32)
+// or 16-byte (FP64) accesses are served together, so the layouts are chosen
+// against a model of the 32 four-byte banks per half-warp, over every store
+// and load of every Stockham exchange of the compiled plans:
 //  MAP 0 (c fastest in a warp): odd line pitch (FP32, N = 256: one pad slot
-//        every 16 elements and two between lines).
+//        every 8 elements and a pitch of N + N/8 + 2).
+//  MAP 1 (t fastest in a warp): FP32, N = 128 / 192 / 256: the low four index
+//        bits XOR-ed with a key linear in the higher bits (conflict-free, no
+//        padding); otherwise one pad slot every 2^SH elements (conflict-free
+//        except FP32 N = 96 and 160: 1.33 and 1.67 wavefronts per request).
 template <class T, int N, int MAP> struct SIdx {
-    static constexpr int SH = MAP == 1 ? ((N == 128 || N == 256) ? 4 : 3) : 4;
-    static constexpr bool PADDED = MAP == 1 || (sizeof(T) == 4 && N == 256);
-    static constexpr int LP = PADDED ? N + (N >> SH) + (MAP == 1 ? 0 : 2) : N + 1;
-    static __device__ __forceinline__ int at(int c, int p) { return PADDED ? c * LP + p + (p >> SH) : c * LP + p; }
+    static constexpr bool F32 = sizeof(T) == 4;
+    static constexpr int KIND = MAP == 0 ? ((F32 && N == 256) ? 1 : 0)
+                                         : ((F32 && (N == 128 || N == 192 || N == 256)) ? 2 : 1);
+    static constexpr int SH = MAP == 0 ? 3
+                                       : (F32 ? (N == 96 ? 4 : (N == 160 ? 2 : 3))
+                                              : ((N == 128 || N == 256) ? 4 : 3));
+    static constexpr int LP = KIND == 0 ? N + 1
+                                        : (KIND == 2 ? N
+                                                     : N + (N >> SH) + ((MAP == 0 || (F32 && N == 96)) ? 2 : 0));
+    static __device__ __forceinline__ int swz(int p) {
+        if constexpr (N == 128) {
+            const int q = p >> 4;
+            return p ^ ((q & 1) ^ (((q >> 1) & 1) * 10) ^ (q & 4));
+        } else if constexpr (N == 256) {
+            return p ^ ((p >> 3) & 15);
+        } else {
+            return p ^ ((p >> 2) & 15);
+        }
+    }
+    static __device__ __forceinline__ int at(int c, int p) {
+        if constexpr (KIND == 0) return c * LP + p;
+        else if constexpr (KIND == 1) return c * LP + p + (p >> SH);
+        else return c * LP + swz(p);
+    }
 };
 
 template <class T, int N, int E, int TPL, int RADS, int S, int NS, int MAP>
