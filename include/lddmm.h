@@ -61,6 +61,7 @@ typedef enum {
 enum { LDDMM_F64 = 0, LDDMM_F32 = 1, LDDMM_BF16 = 2 };          /* number types   */
 enum { LDDMM_INTERP_CUBIC = 0, LDDMM_INTERP_LINEAR = 1 };       /* SL interpolant */
 enum { LDDMM_SPACE_V = 0, LDDMM_SPACE_L2 = 1 };                 /* metric of g, Hv */
+enum { LDDMM_OPT_GN = 0, LDDMM_OPT_GD = 1 };                     /* lddmm_register  */
 
 typedef struct {
     int n[3];        /* grid points per axis                                  */
@@ -91,6 +92,8 @@ typedef struct {
     int dealias;         /* 1 (default): 2/3-rule projector P on the products of
                             the EPDiff and Jacobi equations, modes |k_a| <=
                             (n_a - 1)/3 kept; 0: unfiltered products           */
+    int optimizer;       /* LDDMM_OPT_GN (default): Gauss-Newton-Krylov;
+                            LDDMM_OPT_GD: gradient descent in V (Sec. 2.2) */
 } lddmm_params;
 
 #define LDDMM_TRACE_MAX 64
@@ -109,7 +112,7 @@ typedef struct lddmm_handle lddmm_handle;
 
 /* Fill *p with the defaults: alpha 0.01, s 2, weight 1e-3, nt 10, cubic, V,
  * F64 compute and states, checkpoint 1, 5 GN x 10 PCG, rtol 0.1, c1 1e-4,
- * 10 halvings, dealiasing on. */
+ * 10 halvings, dealiasing on, Gauss-Newton. */
 void lddmm_default_params(lddmm_params *p);
 
 /* Device bytes that lddmm_create would allocate for (g, p); 0 if invalid.
@@ -187,7 +190,11 @@ lddmm_status lddmm_jacobian_det(lddmm_handle *h, const void *u, void *J, double 
 
 /* Inexact Gauss-Newton-Krylov registration (Sec. 3): gn_maxit iterations of
  * gradient -> PCG (preconditioner K, Hv per iteration, FP64 scalars) ->
- * Armijo backtracking -> v0 <- v0 + eps dv0.  v0_inout [3][N] is the start
+ * Armijo backtracking -> v0 <- v0 + eps dv0.  With optimizer LDDMM_OPT_GD the
+ * same loop takes the gradient-descent step in V of Sec. 2.2 instead,
+ * v0 <- v0 - eps K g_L2 (no PCG): Armijo backtracking starts at the step that
+ * moves max |K g_L2| by one voxel (min_a h_a) in the first iteration and at
+ * twice the last accepted step afterwards.  v0_inout [3][N] is the start
  * and receives the result.  report (host, nullable) receives the Sec. 4
  * metrics and the per-iteration trace.  Synchronises.  Returns
  * LDDMM_WARN_LINESEARCH (not sticky) when a line search failed. */
@@ -226,6 +233,18 @@ lddmm_status lddmm_apply_metric_noalloc(const lddmm_grid *g, double alpha, int s
                                         const void *in, void *out, int ncomp, void *cuda_stream);
 size_t lddmm_apply_metric_noalloc_scratch_bytes(const lddmm_grid *g, int dtype);
 size_t lddmm_apply_metric_noalloc_capacity(void);
+
+/* FP64 fused multiply-add rate probe (measurement; no counterpart in the
+ * paper).  Launches `blocks` blocks of lddmm_probe_fp64_fma_threads() threads
+ * on `cuda_stream`; every thread runs `iters` rounds of independent FP64 FMA
+ * chains and writes one double to out[thread] (caller-owned device buffer of
+ * blocks * threads doubles).  lddmm_probe_fp64_fma_flops gives the launch's
+ * flop count (2 per FMA); time the launch with CUDA events to get the FP64
+ * rate that bounds the plain FP64 method's FFT passes.  Returns
+ * LDDMM_ERR_ARG for a null buffer or non-positive sizes. */
+lddmm_status lddmm_probe_fp64_fma(double *out, int blocks, int iters, void *cuda_stream);
+double lddmm_probe_fp64_fma_flops(int blocks, int iters);
+int lddmm_probe_fp64_fma_threads(void);
 
 #ifdef __cplusplus
 }

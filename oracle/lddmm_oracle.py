@@ -555,3 +555,56 @@ def register(g: Grid, p: Params, I0, I1, v0=None, gn_maxit=5, pcg_maxit=10, pcg_
     J = jacobian_det(g, trf.u)
     return GNReport(energies=energies, pcg_iters=iters, steps=steps, gnorm_rel=gnorm_rel,
                     mse_rel=float(mse), jac_min=float(J.min()), jac_max=float(J.max()), v0=v)
+
+
+def register_gd(g: Grid, p: Params, I0, I1, v0=None, maxit=50, c1=1e-4, ls_maxit=10, replay=None):
+    """Gradient descent in V on E(v0), the optimisation of Sec. 2.2:
+    v0 <- v0 - eps grad_V E with grad_V E = K g_L2 (the V-Riesz representer of
+    the reduced gradient).  The paper gives no step rule; this reading uses
+    Armijo backtracking with halving, starting in the first iteration at the
+    step that moves max |K g_L2| by one voxel (min_a h_a) and afterwards at
+    twice the last accepted step.
+
+    ``replay`` = list of eps per iteration forces the steps.
+    """
+    v = np.zeros((3,) + g.n) if v0 is None else np.array(v0, dtype=np.float64)
+    energies, iters, steps = [], [], []
+    g0max = None
+    eps_prev = None
+    hmin = min(g.h)
+    for n_it in range(maxit):
+        gl2, E, _, _, _ = gradient(g, p, v, I0, I1)
+        energies.append(E)
+        gV = g.K(gl2)
+        if g0max is None:
+            g0max = float(np.abs(gV if p.space == "V" else gl2).max())
+        x = -gV
+        slope = g.dot(gl2, x)
+        iters.append(0)
+        if replay is not None:
+            eps = replay[n_it]
+        else:
+            kgmax = float(np.abs(gV).max())
+            eps = (hmin / kgmax if kgmax > 0 else 1.0) if eps_prev is None else 2.0 * eps_prev
+            accepted = False
+            for _ in range(ls_maxit):
+                Et = energy(g, p, v + eps * x, I0, I1)[0]
+                if Et <= E + c1 * eps * slope:
+                    accepted = True
+                    break
+                eps *= 0.5
+            if not accepted:
+                eps = 0.0
+        steps.append(eps)
+        if eps == 0.0:
+            break
+        eps_prev = eps
+        v = v + eps * x
+    Ef, _, _, trf = energy(g, p, v, I0, I1)
+    energies.append(Ef)
+    gl2f = gradient(g, p, v, I0, I1)[0]
+    gnorm_rel = float(np.abs(to_space(g, p, gl2f)).max() / g0max) if g0max else 0.0
+    mse = g.dot(trf.m1 - I1, trf.m1 - I1) / g.dot(I0 - I1, I0 - I1)
+    J = jacobian_det(g, trf.u)
+    return GNReport(energies=energies, pcg_iters=iters, steps=steps, gnorm_rel=gnorm_rel,
+                    mse_rel=float(mse), jac_min=float(J.min()), jac_max=float(J.max()), v0=v)

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "lib", "liblddmm.so")
 LDDMM_F64, LDDMM_F32, LDDMM_BF16 = 0, 1, 2
 LDDMM_INTERP_CUBIC, LDDMM_INTERP_LINEAR = 0, 1
 LDDMM_SPACE_V, LDDMM_SPACE_L2 = 0, 1
+LDDMM_OPT_GN, LDDMM_OPT_GD = 0, 1
 LDDMM_TRACE_MAX = 64
 
 STATUS = {
@@ -40,7 +41,7 @@ class lddmm_params(ctypes.Structure):
         ("compute_dtype", ctypes.c_int), ("state_dtype", ctypes.c_int),
         ("checkpoint_every", ctypes.c_int), ("gn_maxit", ctypes.c_int), ("pcg_maxit", ctypes.c_int),
         ("pcg_rtol", ctypes.c_double), ("armijo_c1", ctypes.c_double), ("ls_maxit", ctypes.c_int),
-        ("dealias", ctypes.c_int),
+        ("dealias", ctypes.c_int), ("optimizer", ctypes.c_int),
     ]
 
 
@@ -95,6 +96,9 @@ SIGNATURES = {
                                                   ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "lddmm_apply_metric_noalloc_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(lddmm_grid), ctypes.c_int]),
     "lddmm_apply_metric_noalloc_capacity": (ctypes.c_size_t, []),
+    "lddmm_probe_fp64_fma": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "lddmm_probe_fp64_fma_flops": (ctypes.c_double, [ctypes.c_int, ctypes.c_int]),
+    "lddmm_probe_fp64_fma_threads": (ctypes.c_int, []),
 }
 
 
@@ -165,6 +169,33 @@ def apply_metric_noalloc(x, out, power, alpha, s=2, lengths=None, stream=None):
         _check(lib().lddmm_apply_metric_noalloc(ctypes.byref(g), float(alpha), int(s), int(power), dtype,
                                                 _P(x.data_ptr()), _P(out.data_ptr()), ncomp,
                                                 _P(st.cuda_stream)), "lddmm_apply_metric_noalloc")
+
+
+def probe_fp64_fma(device=None, blocks=None, iters=4096, reps=5) -> float:
+    """Measured FP64 FMA rate in TFLOP/s (lddmm_probe_fp64_fma, CUDA events,
+    best of `reps` launches after one warm-up)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    if blocks is None:
+        blocks = 8 * torch.cuda.get_device_properties(dev).multi_processor_count
+    thr = lib().lddmm_probe_fp64_fma_threads()
+    out = torch.empty(blocks * thr, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    best = None
+    with torch.cuda.device(dev):
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _check(lib().lddmm_probe_fp64_fma(_P(out.data_ptr()), blocks, iters, _P(st.cuda_stream)),
+                   "lddmm_probe_fp64_fma")
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            if r > 0:
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+    if not torch.isfinite(out).all():
+        raise LddmmError(6, "lddmm_probe_fp64_fma")
+    return lib().lddmm_probe_fp64_fma_flops(blocks, iters) / (best * 1e-3) / 1e12
 
 
 class Handle:

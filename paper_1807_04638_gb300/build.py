@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblddmm.so")
 
-SOURCES = ["capi.cu", "engine_f64.cu", "engine_f32.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "engine_f64.cu", "engine_f32.cu", "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

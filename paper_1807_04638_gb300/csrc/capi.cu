@@ -24,6 +24,7 @@ static bool params_ok(const lddmm_params* p) {
     if (p->checkpoint_every < 1) return false;
     if (p->gn_maxit < 0 || p->pcg_maxit < 0 || p->ls_maxit < 1) return false;
     if (p->dealias != 0 && p->dealias != 1) return false;
+    if (p->optimizer != LDDMM_OPT_GN && p->optimizer != LDDMM_OPT_GD) return false;
     return true;
 }
 
@@ -46,6 +47,7 @@ void lddmm_default_params(lddmm_params* p) {
     p->armijo_c1 = 1e-4;
     p->ls_maxit = 10;
     p->dealias = 1;
+    p->optimizer = LDDMM_OPT_GN;
 }
 
 size_t lddmm_workspace_bytes(const lddmm_grid* g, const lddmm_params* p) {

@@ -1488,7 +1488,57 @@ class Engine : public EngineBase {
         bool ls_fail = false;
         const int maxit = std::min(prm.gn_maxit, LDDMM_TRACE_MAX);
         int it = 0;
-        for (; it < maxit; ++it) {
+        double eps_prev = 0.0;
+        for (; it < maxit && prm.optimizer == LDDMM_OPT_GD; ++it) {
+            // gradient descent in V (Sec. 2.2): v0 <- v0 - eps K g_L2
+            gradient_core(v, I0, I1, pg, LDDMM_SPACE_L2);
+            if (fetch(0, prm.nt + 3) != LDDMM_OK) return status;
+            const double E = hres[prm.nt + 2] + prm.weight * hres[prm.nt + 1];
+            if (!std::isfinite(E)) return fail(LDDMM_ERR_NONFINITE);
+            R.energy[it] = E;
+            kapply(pg, pz);
+            minmax_async(pz, n3, 60);
+            if (fetch(60, 1) != LDDMM_OK) return status;
+            const double kgmax = hres[60];  // max |K g_L2|: sets the first trial step
+            double gmax = kgmax;            // |g|_inf in the chosen metric
+            if (prm.space == LDDMM_SPACE_L2) {
+                minmax_async(pg, n3, 60);
+                if (fetch(60, 1) != LDDMM_OK) return status;
+                gmax = hres[60];
+            }
+            if (it == 0) g0max = gmax;
+            {
+                PScope ps_(this, KC_MISC, 3.0 * n3 * sizeof(T));
+                k_lincomb2<T><<<g, PW_THREADS, 0, st>>>((T)-1, pz, (T)0, pz, px, n3);
+            }
+            const double slope = dot_now(pg, px, n3);
+            const double hmin = std::min(d.h[0], std::min(d.h[1], d.h[2]));
+            double eps = it == 0 ? (kgmax > 0 ? hmin / kgmax : 1.0) : 2.0 * eps_prev;
+            bool ok = false;
+            for (int t = 0; t < prm.ls_maxit; ++t) {
+                {
+                    PScope ps_(this, KC_MISC, 3.0 * n3 * sizeof(T));
+                    k_lincomb2<T><<<g, PW_THREADS, 0, st>>>((T)1, v, (T)eps, px, pvt, n3);
+                }
+                const double Et = energy_at(pvt, I0, I1);
+                if (status != LDDMM_OK) return status;
+                if (std::isfinite(Et) && Et <= E + prm.armijo_c1 * eps * slope) {
+                    ok = true;
+                    break;
+                }
+                eps *= 0.5;
+            }
+            R.pcg_iters[it] = 0;
+            R.step[it] = ok ? eps : 0.0;
+            if (!ok) {
+                ls_fail = true;
+                ++it;
+                break;
+            }
+            eps_prev = eps;
+            cudaMemcpyAsync(v, pvt, n3 * sizeof(T), cudaMemcpyDeviceToDevice, st);
+        }
+        for (; it < maxit && prm.optimizer == LDDMM_OPT_GN; ++it) {
             gradient_core(v, I0, I1, pg, LDDMM_SPACE_L2);
             if (fetch(0, prm.nt + 3) != LDDMM_OK) return status;
             const double E = hres[prm.nt + 2] + prm.weight * hres[prm.nt + 1];

@@ -53,8 +53,8 @@ class Result:
 
 
 def _key(n, p: N.lddmm_params, lengths):
-    return (tuple(n), p.compute_dtype, p.nt, tuple(lengths) if lengths else None,
-            p.alpha, p.s, p.weight, p.interp, p.space, p.dealias, p.gn_maxit, p.pcg_maxit, p.pcg_rtol)
+    # a parked handle is reused only for exactly the same grid and parameters
+    return (tuple(n), tuple(lengths) if lengths else None) + tuple(getattr(p, f) for f, _ in p._fields_)
 
 
 class Server:

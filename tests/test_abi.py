@@ -56,3 +56,7 @@ def test_host_side_checks_without_gpu(libpath):
     assert lib.lddmm_create(None, ctypes.byref(g), ctypes.byref(p), None) == 1  # ARG
     assert lib.lddmm_shoot(None, None, None, None, None, None) == 1
     assert lib.lddmm_status_string(5).decode().startswith("no linearisation")
+    # the FP64 rate probe checks its arguments before launching
+    assert lib.lddmm_probe_fp64_fma(None, 1, 1, None) == 1
+    thr = lib.lddmm_probe_fp64_fma_threads()
+    assert lib.lddmm_probe_fp64_fma_flops(3, 5) == 2 * 8 * 5 * thr * 3

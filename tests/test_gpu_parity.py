@@ -187,6 +187,24 @@ def test_register_replays_oracle(pkg, interp):
     assert abs(rep["mse_rel"] - ref.mse_rel) < 1e-9 and abs(rep["jac_min"] - ref.jac_min) < 1e-9
 
 
+def test_register_gradient_descent_matches_oracle(pkg):
+    """Gradient descent in V (optimizer LDDMM_OPT_GD): the FP64 GPU run takes
+    the oracle's Armijo steps and reaches its v0."""
+    n = (16, 12, 10)
+    nt = 4
+    g, I0, I1, vtrue = problem(n, 12, nt)
+    p = O.Params(nt=nt)
+    with pkg.Handle(n, params(pkg, "f64", nt=nt, gn_maxit=6, optimizer=pkg.LDDMM_OPT_GD)) as h:
+        v = torch.zeros((3,) + n, dtype=torch.float64, device="cuda")
+        rep = h.lddmm_register(dev(I0, torch.float64), dev(I1, torch.float64), v)
+    ref = O.register_gd(g, p, I0, I1, maxit=6)
+    assert rep["pcg_iters"] == [0] * 6 and rep["pcg_iters_total"] == 0
+    assert np.allclose(rep["step"], ref.steps, rtol=1e-9, atol=0)
+    assert rel(host(v), ref.v0) < 1e-9
+    assert np.allclose(rep["energy"], ref.energies, rtol=1e-9)
+    assert abs(rep["mse_rel"] - ref.mse_rel) < 1e-9 and abs(rep["gnorm_rel"] - ref.gnorm_rel) < 1e-9
+
+
 def test_errors_are_reported(pkg):
     n = (8, 8, 8)
     with pytest.raises(pkg.LddmmError):
@@ -224,3 +242,10 @@ def test_unfiltered_products_option(pkg, prec):
     assert abs(e[0] - E) < tol * abs(E)
     assert rel(host(grad), O.to_space(g, p, gl2)) < tol
     assert rel(host(hv), O.to_space(g, p, hl2)) < tol
+
+
+def test_fp64_fma_probe(pkg):
+    """The FP64 rate probe runs, writes finite values and reports a rate
+    within loose sanity bounds (not a performance assertion)."""
+    tf = pkg.probe_fp64_fma(iters=256, reps=2)
+    assert 0.01 < tf < 200.0

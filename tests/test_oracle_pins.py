@@ -446,6 +446,39 @@ def test_gauss_newton_decreases_energy_and_replays():
     assert rel(again.v0, rep.v0) < 1e-14
 
 
+def test_gradient_descent_in_V_steps_and_armijo():
+    """Gradient descent in V (Sec. 2.2): every accepted step moves along
+    -K g_L2 with g_L2 the reduced gradient, satisfies the Armijo condition
+    recomputed from the energy, decreases E; the first trial step moves
+    max |K g| by one voxel, so the first accepted step is that times 2^-k;
+    a replay reproduces the iterates."""
+    g = O.Grid((8, 8, 8), alpha=0.02)
+    p = O.Params(alpha=0.02, nt=4, weight=1e-3)
+    I0, vtrue = synth.blob_pair_inputs(g.n, 96, kmax=2, max_disp_vox=1.0)
+    I0 = synth.spectral_gaussian_smooth(I0, 1.0)
+    I1 = O.shoot(g, vtrue, p.nt, I0).m1
+    rep = O.register_gd(g, p, I0, I1, maxit=4)
+    assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
+    assert rep.pcg_iters == [0] * len(rep.steps)
+    # first step: h / max|K g(0)| halved an integer number of times; at v0 = 0
+    # the gradient is the closed form P(-2 (I0 - I1) grad I0)
+    g0 = g.P(-2.0 * (I0 - I1)[None] * g.grad(I0))
+    k0 = float(np.abs(g.K(g0)).max())
+    ratio = rep.steps[0] / (min(g.h) / k0)
+    assert abs(np.log2(ratio) - round(np.log2(ratio))) < 1e-9 and ratio <= 1.0
+    # replay the steps one at a time and check Armijo along -K g_L2
+    v = np.zeros((3,) + g.n)
+    for eps in rep.steps:
+        gl2, E = O.gradient(g, p, v, I0, I1)[:2]
+        x = -g.K(gl2)
+        Et = O.energy(g, p, v + eps * x, I0, I1)[0]
+        assert Et <= E + 1e-4 * eps * g.dot(gl2, x)
+        v = v + eps * x
+    assert rel(v, rep.v0) < 1e-14
+    again = O.register_gd(g, p, I0, I1, maxit=4, replay=rep.steps)
+    assert rel(again.v0, rep.v0) < 1e-14
+
+
 @pytest.mark.parametrize("n", [(20, 12, 18), (12, 10, 15), (128, 128, 128), (256, 300, 256)])
 def test_dealias_band_count_closed_form(n):
     """P keeps exactly (2K0+1)(2K1+1)(K2+1) half-spectrum modes, K_a = (n_a-1)//3,
