@@ -608,3 +608,53 @@ def register_gd(g: Grid, p: Params, I0, I1, v0=None, maxit=50, c1=1e-4, ls_maxit
     J = jacobian_det(g, trf.u)
     return GNReport(energies=energies, pcg_iters=iters, steps=steps, gnorm_rel=gnorm_rel,
                     mse_rel=float(mse), jac_min=float(J.min()), jac_max=float(J.max()), v0=v)
+
+
+# ---------------------------------------------------------------------------
+# Cross-check of the linearised final image (Sec. 3, incremental state
+# equation): the literal route, for comparison with delta m(1) = -grad m(1) .
+# xi(1) used by the sweeps.  Not part of the path.
+# ---------------------------------------------------------------------------
+
+def tangent_path(g: Grid, tr: Trajectory, delta):
+    """The tangent sweep of ``tangent``, returning eta_k for k = 0..nt and
+    xi_nt (the same Heun steps)."""
+    dt = 1.0 / tr.nt
+    eta = g.P(delta)
+    xi = np.zeros_like(eta)
+    etas = [eta]
+    for k in range(tr.nt):
+        be, bx = jacobi_A(g, tr.v[k], eta, xi)
+        es, xs = eta + dt * be, xi + dt * bx
+        ce, cx = jacobi_A(g, tr.vstar[k], es, xs)
+        eta = eta + 0.5 * dt * (be + ce)
+        xi = xi + 0.5 * dt * (bx + cx)
+        etas.append(eta)
+    return etas, xi
+
+
+def incremental_state_literal(g: Grid, tr: Trajectory, I0, etas, kind="cubic"):
+    """delta m(1) from the incremental state equation of Sec. 3,
+      d/dt delta m + grad(delta m) . v + grad m . delta v = 0,  delta m(0) = 0,
+    with delta v = eta (the incremental EPDiff solution) and m_t = I0 o psi_t.
+    Along the characteristics of the map step (departure point X of
+    ``sl_map_step``) the equation reads d/dt delta m = -grad m . eta, which is
+    integrated by the trapezoidal rule:
+      dm_{k+1}(x) = dm_k(X) - dt/2 [(grad m_{k+1} . eta_{k+1})(x)
+                                    + (grad m_k . eta_k)(X)]."""
+    dt = 1.0 / tr.nt
+    h = np.array(g.h).reshape(3, 1, 1, 1)
+    x = g.coords
+    u = np.zeros((3,) + g.n)
+    src = np.sum(g.grad(I0) * etas[0], axis=0)
+    dm = np.zeros(g.n)
+    for k in range(tr.nt):
+        v0_, v1_ = tr.v[k], tr.v[k + 1]
+        u = sl_map_step(g, u, v0_, v1_, dt, kind)
+        m1_ = warp(g, I0, u, kind)
+        src1 = np.sum(g.grad(m1_) * etas[k + 1], axis=0)
+        vt = interp(v0_, x - dt * v1_ / h, kind)
+        X = x + (-0.5 * dt * (v1_ + vt)) / h
+        dm = interp(dm, X, kind) - 0.5 * dt * (src1 + interp(src, X, kind))
+        src = src1
+    return dm
