@@ -76,16 +76,25 @@ __device__ __forceinline__ double sym_div(double a, double b) { return a / b; }
 template <class T>
 __device__ __forceinline__ cpx<T> sym_apply(const SymT<T>& sy, const SpecTabs<T>& tb, int k0, int k1, int k2, cpx<T> v) {
     if (sy.mask) {
-        const int a0 = k0 <= tb.n[0] / 2 ? k0 : tb.n[0] - k0;
-        const int a1 = k1 <= tb.n[1] / 2 ? k1 : tb.n[1] - k1;
-        if (a0 > tb.kcut[0] || a1 > tb.kcut[1] || k2 > tb.kcut[2]) return mk((T)0, (T)0);
+        // |k_a| > kcut_a  <=>  kcut_a < k_a < n_a - kcut_a (index k_a in [0, n_a))
+        const bool out0 = k0 > tb.kcut[0] && k0 < tb.n[0] - tb.kcut[0];
+        const bool out1 = k1 > tb.kcut[1] && k1 < tb.n[1] - tb.kcut[1];
+        if (out0 || out1 || k2 > tb.kcut[2]) return mk((T)0, (T)0);
     }
     T f = sy.scale;
     if (sy.lpow != 0) {
-        T base = (T)1 + tb.alpha * (tb.ksq[0][k0] + tb.ksq[1][k1] + tb.ksq[2][k2]);
-        int e = tb.s * (sy.lpow > 0 ? sy.lpow : -sy.lpow);
-        T p = (T)1;
-        for (int q = 0; q < e; ++q) p *= base;
+        const T base = (T)1 + tb.alpha * (tb.ksq[0][k0] + tb.ksq[1][k1] + tb.ksq[2][k2]);
+        const int e = tb.s * (sy.lpow > 0 ? sy.lpow : -sy.lpow);
+        T p;
+        if (e == 2) {
+            p = base * base;
+        } else if (e == 4) {
+            p = base * base;
+            p = p * p;
+        } else {
+            p = (T)1;
+            for (int q = 0; q < e; ++q) p *= base;
+        }
         f = sy.lpow > 0 ? f * p : sym_div(f, p);
     }
     if (sy.deriv >= 0) {
@@ -152,6 +161,27 @@ template <class T> inline PassJobT<T> to_jobt(const PassJob& j) {
     return r;
 }
 
+// Division by a divisor d (1 <= d < 2^24) fixed for a launch, for numerators
+// n < 2^24, by one 32 x 32 -> 64-bit multiply and a shift: with
+// l = ceil(log2 d), sh = 24 + l and m = ceil(2^sh / d) (m < 2^26), n / d =
+// (n m) >> sh exactly, since 2^sh <= m d <= 2^sh + 2^l (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994,
+// Thm. 4.2).  Built on the host; the kernels only multiply.
+struct FastDiv {
+    unsigned d, m;
+    int sh;
+    FastDiv() : d(1), m(1u << 24), sh(24) {}
+    explicit FastDiv(unsigned dd) : d(dd) {
+        int l = 0;
+        while ((1u << l) < dd) ++l;
+        sh = 24 + l;
+        m = (unsigned)(((1ull << sh) + dd - 1) / dd);
+    }
+    __device__ __forceinline__ unsigned div(unsigned n) const {
+        return (unsigned)(((unsigned long long)n * m) >> sh);
+    }
+};
+
 template <class T> struct PassParams {
     FFTAxis ax;
     int n0, n1, n2, n2h;
@@ -162,6 +192,9 @@ template <class T> struct PassParams {
     // other spectral entry is treated as zero on input and left unwritten on
     // output.  The full transform has nb2 = n2h, c1 = s1 = n1.
     int nb2, c1, s1;
+    // register-blocked C2C passes: divisions by the launch's tile count, by
+    // the tiles per k2 plane (axis 0) and by n0 (axis 1)
+    FastDiv fd_tiles, fd_tpk, fd_n0;
     SpecTabs<T> tabs;
     int njobs;
     PassJobT<T> jobs[MAXJOBS];

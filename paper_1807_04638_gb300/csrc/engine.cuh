@@ -207,11 +207,16 @@ template <class T> struct FastPass {
             if (set_attr) return raise_smem_limit(k_fast_c2c<T, N, 1>, sm);
             (void)n2h;
             const int ntiles = (int)(((size_t)pp.nb2 * n0 + TL - 1) / TL);
+            pp.fd_tiles = FastDiv((unsigned)ntiles);
+            pp.fd_n0 = FastDiv((unsigned)n0);
             k_fast_c2c<T, N, 1><<<persistent_grid(ntiles * nj), FAST_THREADS, sm, st>>>(pp, ntiles);
         } else {
             const size_t sm = fast_c2c_smem<T, N>(0);
             if (set_attr) return raise_smem_limit(k_fast_c2c<T, N, 0>, sm);
-            const int ntiles = pp.nb2 * ((pp.c1 + TL - 1) / TL + (n1 - pp.s1 + TL - 1) / TL);
+            const int tpk = (pp.c1 + TL - 1) / TL + (n1 - pp.s1 + TL - 1) / TL;
+            const int ntiles = pp.nb2 * tpk;
+            pp.fd_tiles = FastDiv((unsigned)ntiles);
+            pp.fd_tpk = FastDiv((unsigned)tpk);
             k_fast_c2c<T, N, 0><<<persistent_grid(ntiles * nj), FAST_THREADS, sm, st>>>(pp, ntiles);
         }
         return true;

@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
             k2t = 0;
             kb = line0;
         } else {
-            k2t = tile / tpk;
-            const int r = tile % tpk;
+            k2t = (int)pp.fd_tpk.div((unsigned)tile);
+            const int r = tile - k2t * tpk;
             if (r < tA) {
                 kb = r * TL;
                 nval = min(TL, c1 - kb);
@@ -242,12 +242,19 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
     // AXIS 1 inverse: spectral entries k1 in [c1, s1) are zero (not read)
     auto k1_out = [&](int p) { return AXIS == 1 && p >= c1 && p < s1; };
     // issue the copy of input q of item w into stage buffer sb
+    // work item w -> (job, tile)
+    auto split = [&](int w, int& jw, int& tile) {
+        jw = (int)pp.fd_tiles.div((unsigned)w);
+        tile = w - jw * ntiles;
+    };
     auto issue = [&](int w, int q, int sb) {
         if (w < nitems) {
-            const PassJobT<T>& jb = pp.jobs[w / ntiles];
+            int jw, tl;
+            split(w, jw, tl);
+            const PassJobT<T>& jb = pp.jobs[jw];
             const cpx<T>* src = (const cpx<T>*)jb.in[q];
             int g0, nval, k2t, kb;
-            tile_geo(w % ntiles, g0, nval, k2t, kb);
+            tile_geo(tl, g0, nval, k2t, kb);
             if (AXIS == 1) {
                 const int chunks = nval * N * (int)sizeof(cpx<T>) / 16;
                 const bool skip = pp.sign > 0 && c1 < s1;
@@ -257,10 +264,14 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
                     cp_async16((char*)(stage0 + sb * G::TILE) + 16 * i, (const char*)(src + g0) + 16 * i);
                 }
             } else {
-                const int cpr = nval * (int)sizeof(cpx<T>) / 16;  // 16-byte chunks per row
-                for (int i = threadIdx.x; i < N * cpr; i += FAST_THREADS) {
-                    const int p = i / cpr, ch = i % cpr;
-                    cp_async16((char*)((stage0 + sb * G::TILE) + p * TL) + 16 * ch, (const char*)(src + g0 + p * n1) + 16 * ch);
+                // 16-byte chunks per row: CPR for a full tile (compile time), cpr valid
+                constexpr int CPR = TL * (int)sizeof(cpx<T>) / 16;
+                const int cpr = nval * (int)sizeof(cpx<T>) / 16;
+                for (int i = threadIdx.x; i < N * CPR; i += FAST_THREADS) {
+                    const int p = i / CPR, ch = i % CPR;
+                    if (ch < cpr)
+                        cp_async16((char*)((stage0 + sb * G::TILE) + p * TL) + 16 * ch,
+                                   (const char*)(src + g0 + p * n1) + 16 * ch);
                 }
             }
         }
@@ -271,7 +282,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
     int w = blockIdx.x, q = 0, sb = 0;
     int nw = w, nq = 0;  // the unit being prefetched
     auto advance = [&](int& ww, int& qq) {
-        const PassJobT<T>& jb = pp.jobs[ww / ntiles];
+        const PassJobT<T>& jb = pp.jobs[pp.fd_tiles.div((unsigned)ww)];
         if (++qq >= jb.nin) {
             qq = 0;
             ww += gridDim.x;
@@ -286,18 +297,19 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
         else cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        const int jw = w / ntiles;
+        int jw, tl;
+        split(w, jw, tl);
         const PassJobT<T>& job = pp.jobs[jw];
         int g0, nval, k2t, kb;
-        tile_geo(w % ntiles, g0, nval, k2t, kb);
+        tile_geo(tl, g0, nval, k2t, kb);
         const bool valid = c < nval;
         const cpx<T>* tile = (stage0 + sb * G::TILE);
         // frequency indices of the other two axes for this thread's line
         int k0b, k1b, k2b;
         if (AXIS == 1) {
             const int line = kb + (valid ? c : 0);
-            k2b = line / n0;
-            k0b = line % n0;
+            k2b = (int)pp.fd_n0.div((unsigned)line);
+            k0b = line - k2b * n0;
             k1b = 0;
         } else {
             k2b = k2t;
