@@ -339,9 +339,10 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
                     }
                     fast_fft<T, N, MAP>(x, b0, b1, c, t, tw, +1);
                     if (valid) {
-                        cpx<T>* out = (cpx<T>*)job.out[o];
+                        cpx<T>* ob = (cpx<T>*)job.out[o] + gidx(t);
+                        const int sm = AXIS == 1 ? TPL : TPL * n1;  // element step between m
 #pragma unroll
-                        for (int m = 0; m < E; ++m) out[gidx(t + TPL * m)] = x[m];
+                        for (int m = 0; m < E; ++m) ob[m * sm] = x[m];
                     }
                 }
             }
@@ -359,15 +360,19 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
                 acc[m] = q == 0 ? v : acc[m] + v;
             }
             if (last && valid) {
-                cpx<T>* out = (cpx<T>*)job.out[0];
+                const int g0t = gidx(t);
+                const int sm = AXIS == 1 ? TPL : TPL * n1;  // element step between m
+                for (int b = 0; b < job.nb; ++b) {
+                    const cpx<T>* bp = (const cpx<T>*)job.base[b] + g0t;
+                    const T bc = job.bcoef[b];
 #pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    if (k1_out(t + TPL * m)) continue;  // outside the band: not written
-                    const int g = gidx(t + TPL * m);
-                    cpx<T> v = acc[m];
-                    for (int b = 0; b < job.nb; ++b) v = v + job.bcoef[b] * ((const cpx<T>*)job.base[b])[g];
-                    out[g] = v;
+                    for (int m = 0; m < E; ++m)
+                        if (!k1_out(t + TPL * m)) acc[m] = acc[m] + bc * bp[m * sm];
                 }
+                cpx<T>* ob = (cpx<T>*)job.out[0] + g0t;
+#pragma unroll
+                for (int m = 0; m < E; ++m)
+                    if (!k1_out(t + TPL * m)) ob[m * sm] = acc[m];  // outside the band: not written
             }
         }
         // next unit
@@ -402,14 +407,27 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
     const int c = threadIdx.x / TPL, t = threadIdx.x % TPL;
     const bool va = 2 * c < nr, vb = 2 * c + 1 < nr;
     cpx<T> x[E];
+    // staging geometry: thread -> (row of the block, first k), KS k per sweep
+    static_assert(FAST_THREADS % (2 * TL) == 0, "rows of a block must tile the threads");
+    constexpr int KS = FAST_THREADS / (2 * TL);
+    const int srow = threadIdx.x % (2 * TL), sk = threadIdx.x / (2 * TL);
+    const bool rv = srow < nr;
+    const int nb2 = pp.nb2;
     if (pp.sign > 0) {
-        for (int e = threadIdx.x; e < 2 * TL * NH; e += FAST_THREADS) {
-            const int row = e % (2 * TL), k = e / (2 * TL);
-            cpx<T> acc = mk((T)0, (T)0);
-            if (row < nr && k < pp.nb2)
-                for (int b = 0; b < job.nin; ++b)
-                    acc = acc + job.isym[b].scale * ((const cpx<T>*)job.in[b])[(size_t)k * rows + r0 + row];
-            H[row * PH + k] = acc;
+        // H[row][k] = sum_b c_b in_b[k][r0 + row] on the band, zero above it
+        if (job.nin == 1) {
+            const cpx<T>* src = (const cpx<T>*)job.in[0] + (r0 + srow);
+            const T c0 = job.isym[0].scale;
+            for (int k = sk; k < NH; k += KS)
+                H[srow * PH + k] = rv && k < nb2 ? c0 * src[k * rows] : mk((T)0, (T)0);
+        } else {
+            for (int k = sk; k < NH; k += KS) {
+                cpx<T> acc = mk((T)0, (T)0);
+                if (rv && k < nb2)
+                    for (int b = 0; b < job.nin; ++b)
+                        acc = acc + job.isym[b].scale * ((const cpx<T>*)job.in[b])[k * rows + r0 + srow];
+                H[srow * PH + k] = acc;
+            }
         }
         for (int o = 0; o < job.nout; ++o) {
             const SymT<T> sy = job.osym[o];
@@ -432,22 +450,20 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
                 x[m] = mk(a.x - b.y, a.y + b.x);
             }
             fast_fft<T, N, 1>(x, b0, b1, c, t, tw, +1);
-            T* out = (T*)job.out[o];
+            T* oa = (T*)job.out[o] + ((r0 + 2 * c) * N + t);  // row pair (2c, 2c + 1)
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                const int p = t + TPL * m;
-                if (va) out[(size_t)(r0 + 2 * c) * N + p] = x[m].x;
-                if (vb) out[(size_t)(r0 + 2 * c + 1) * N + p] = x[m].y;
+                if (va) oa[TPL * m] = x[m].x;
+                if (vb) oa[N + TPL * m] = x[m].y;
             }
         }
     } else {
         for (int q = 0; q < job.nin; ++q) {
-            const T* in = (const T*)job.in[q];
+            const T* ia = (const T*)job.in[q] + ((r0 + 2 * c) * N + t);  // row pair (2c, 2c + 1)
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                const int p = t + TPL * m;
-                const T a = va ? in[(size_t)(r0 + 2 * c) * N + p] : (T)0;
-                const T b = vb ? in[(size_t)(r0 + 2 * c + 1) * N + p] : (T)0;
+                const T a = va ? ia[TPL * m] : (T)0;
+                const T b = vb ? ia[N + TPL * m] : (T)0;
                 x[m] = mk(a, b);
             }
             fast_fft<T, N, 1>(x, b0, b1, c, t, tw, -1);
@@ -457,7 +473,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
             for (int m = 0; m < E; ++m) b0[SIdx<T, N, 1>::at(c, t + TPL * m)] = x[m];
             __syncthreads();
             const SymT<T> sy = job.isym[q];
-            for (int k = t; k < pp.nb2; k += TPL) {
+            for (int k = t; k < nb2; k += TPL) {
                 const cpx<T> zk = b0[SIdx<T, N, 1>::at(c, k)];
                 const cpx<T> zn = cj(b0[SIdx<T, N, 1>::at(c, k == 0 ? 0 : N - k)]);
                 const cpx<T> sa = sym_apply(sy, pp.tabs, 0, 0, k, (T)0.5 * (zk + zn));
@@ -469,11 +485,9 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
             }
         }
         __syncthreads();
-        cpx<T>* out = (cpx<T>*)job.out[0];
-        for (int e = threadIdx.x; e < 2 * TL * pp.nb2; e += FAST_THREADS) {
-            const int row = e % (2 * TL), k = e / (2 * TL);
-            if (row < nr) out[(size_t)k * rows + r0 + row] = H[row * PH + k];
-        }
+        cpx<T>* dst = (cpx<T>*)job.out[0] + (r0 + srow);
+        if (rv)
+            for (int k = sk; k < nb2; k += KS) dst[k * rows] = H[srow * PH + k];
     }
 }
 
