@@ -105,6 +105,17 @@ __device__ __forceinline__ cpx<T> sym_apply(const SymT<T>& sy, const SpecTabs<T>
     return mk(f * v.x, f * v.y);
 }
 
+// The multiplier of sym_apply at one wave vector, for applying the same
+// symbol to several values: (f, 0) or, with a derivative, (0, d f).
+template <class T>
+__device__ __forceinline__ cpx<T> sym_coef(const SymT<T>& sy, const SpecTabs<T>& tb, int k0, int k1, int k2) {
+    return sym_apply(sy, tb, k0, k1, k2, mk((T)1, (T)0));
+}
+// v times such a multiplier (one of its parts is zero)
+template <class T> __device__ __forceinline__ cpx<T> sym_mul(cpx<T> s, cpx<T> v) {
+    return mk(s.x * v.x - s.y * v.y, s.x * v.y + s.y * v.x);
+}
+
 // One FFT axis: length, radix plan, twiddle table e^{-2 pi i t / n}, t < n.
 struct FFTAxis {
     int n;

@@ -437,8 +437,15 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
                 const int k = t + TPL * m;
                 const bool lo = k < NH;
                 const int kk = lo ? k : N - k;
-                cpx<T> a = sym_apply(sy, pp.tabs, 0, 0, kk, H[(2 * c) * PH + kk]);
-                cpx<T> b = sym_apply(sy, pp.tabs, 0, 0, kk, H[(2 * c + 1) * PH + kk]);
+                cpx<T> a, b;
+                if constexpr (sizeof(T) == 4) {
+                    const cpx<T> sc = sym_coef(sy, pp.tabs, 0, 0, kk);  // same for both rows
+                    a = sym_mul(sc, H[(2 * c) * PH + kk]);
+                    b = sym_mul(sc, H[(2 * c + 1) * PH + kk]);
+                } else {  // FP64 is bound by its multiplies: apply the symbol directly
+                    a = sym_apply(sy, pp.tabs, 0, 0, kk, H[(2 * c) * PH + kk]);
+                    b = sym_apply(sy, pp.tabs, 0, 0, kk, H[(2 * c + 1) * PH + kk]);
+                }
                 if (kk == 0 || kk == N / 2) {
                     a.y = 0;
                     b.y = 0;
@@ -476,8 +483,15 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
             for (int k = t; k < nb2; k += TPL) {
                 const cpx<T> zk = b0[SIdx<T, N, 1>::at(c, k)];
                 const cpx<T> zn = cj(b0[SIdx<T, N, 1>::at(c, k == 0 ? 0 : N - k)]);
-                const cpx<T> sa = sym_apply(sy, pp.tabs, 0, 0, k, (T)0.5 * (zk + zn));
-                const cpx<T> sb = sym_apply(sy, pp.tabs, 0, 0, k, rot((T)0.5 * (zk - zn), -1));
+                cpx<T> sa, sb;
+                if constexpr (sizeof(T) == 4) {
+                    const cpx<T> sc = sym_coef(sy, pp.tabs, 0, 0, k);  // same for both rows
+                    sa = sym_mul(sc, (T)0.5 * (zk + zn));
+                    sb = sym_mul(sc, rot((T)0.5 * (zk - zn), -1));
+                } else {
+                    sa = sym_apply(sy, pp.tabs, 0, 0, k, (T)0.5 * (zk + zn));
+                    sb = sym_apply(sy, pp.tabs, 0, 0, k, rot((T)0.5 * (zk - zn), -1));
+                }
                 cpx<T>* ha = &H[(2 * c) * PH + k];
                 cpx<T>* hb = &H[(2 * c + 1) * PH + k];
                 *ha = q == 0 ? sa : *ha + sa;
