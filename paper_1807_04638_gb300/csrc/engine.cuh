@@ -177,9 +177,9 @@ inline bool raise_smem_limit(K kernel, size_t need) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) == cudaSuccess;
 }
 
-// Grid of a persistent pass: three resident blocks per SM, never more blocks
-// than work items.
-inline int persistent_grid(int items) {
+// Grid of a persistent pass: `per_sm` resident blocks per SM, never more
+// blocks than work items.
+inline int persistent_grid(int items, int per_sm = 3) {
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -187,11 +187,29 @@ inline int persistent_grid(int items) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 152;
     }
-    return std::max(1, std::min(items, 3 * sms));
+    return std::max(1, std::min(items, per_sm * sms));
 }
 
 // Launch of the register-blocked passes for the compiled line lengths.
 template <class T> struct FastPass {
+    // the persistent axis-2 kernel's shared-memory limit is raised (per N)
+    template <int N> static bool& a2p_ready() {
+        static bool v = false;
+        return v;
+    }
+    // The persistent axis-2 kernel takes full tiles of r2 rows, one input per
+    // inverse job, and 16-byte aligned inputs (its copies are 16-byte
+    // cp.async of whole rows or plane segments).
+    static bool axis2p_fits(const PassParams<T>& pp, int nj, size_t rows, int r2) {
+        if (rows % (size_t)r2 != 0 || (rows / r2) * (size_t)nj >= (1u << 24)) return false;
+        for (int j = 0; j < nj; ++j) {
+            const PassJobT<T>& jb = pp.jobs[j];
+            if (pp.sign > 0 && jb.nin != 1) return false;
+            for (int i = 0; i < jb.nin; ++i)
+                if ((uintptr_t)jb.in[i] % 16 != 0) return false;
+        }
+        return true;
+    }
     template <int N>
     static bool go(int axis, int sign, PassParams<T>& pp, int nj, size_t rows, int n0, int n1, int n2h,
                    cudaStream_t st, bool set_attr) {
@@ -199,7 +217,20 @@ template <class T> struct FastPass {
         constexpr int TL = FAST_THREADS / (N / FastPlan<N>::E);
         if (axis == 2) {
             const size_t sm = fast_axis2_smem<T, N>();
-            if (set_attr) return raise_smem_limit(k_fast_axis2<T, N>, sm);
+            constexpr bool PERS = sizeof(T) == 4 && FastPlan<N>::E <= 12;
+            if (set_attr) {
+                if constexpr (PERS) a2p_ready<N>() = raise_smem_limit(k_fast_axis2p<T, N>, fast_axis2p_smem<T, N>());
+                return raise_smem_limit(k_fast_axis2<T, N>, sm);
+            }
+            if constexpr (PERS) {
+                if (a2p_ready<N>() && axis2p_fits(pp, nj, rows, 2 * TL)) {
+                    const int ntiles = (int)(rows / (2 * TL));
+                    pp.fd_tiles = FastDiv((unsigned)ntiles);
+                    k_fast_axis2p<T, N><<<persistent_grid(ntiles * nj, A2P_BLOCKS), FAST_THREADS, fast_axis2p_smem<T, N>(),
+                                          st>>>(pp, ntiles);
+                    return true;
+                }
+            }
             const int gx = (int)((rows + 2 * TL - 1) / (2 * TL));
             k_fast_axis2<T, N><<<dim3(gx, nj), FAST_THREADS, sm, st>>>(pp);
         } else if (axis == 1) {

@@ -505,6 +505,187 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
     }
 }
 
+// ---------------------------------------------------------------- axis-2 pass, persistent
+// The transforms of k_fast_axis2 for FP32 grids whose row count is a multiple
+// of the tile (2*TL rows) and whose inverse jobs have one input.  Persistent
+// blocks walk the (tile, job) work items; the next unit's input is staged with
+// cp.async into the other half of a double buffer while the current one is
+// transformed:
+//   inverse: the band planes k2 < nb2 of the tile's rows, S[k][row] with a
+//            16-byte pitch SP, read back as row pairs;
+//   forward: the tile's 2*TL real rows of one input (contiguous), one unit
+//            per input of the job.
+template <class T, int N> struct A2Geom {
+    static constexpr int E = FastPlan<N>::E;
+    static constexpr int TPL = N / E;
+    static constexpr int TL = FAST_THREADS / TPL;
+    static constexpr int R2 = 2 * TL;                          // rows per tile
+    static constexpr int NH = N / 2 + 1;
+    static constexpr int PH = (NH % 2 == 0) ? NH + 1 : NH;     // H pitch (forward)
+    static constexpr int SP = R2 + 16 / (int)sizeof(cpx<T>);   // inverse stage pitch
+    static constexpr int SI = NH * SP;                         // inverse stage (complex)
+    static constexpr int SF = R2 * N / 2;                      // forward stage (complex)
+    static constexpr int XT = TL * SIdx<T, N, 1>::LP;          // one exchange tile
+    static constexpr int SS0 = SI > SF ? SI : SF;
+    static constexpr int SS = SS0 > XT ? SS0 : XT;             // one stage buffer (also an exchange tile)
+    static constexpr int HS = R2 * PH > XT ? R2 * PH : XT;     // H (forward) / b0 (inverse)
+    static constexpr int CPK = R2 * (int)sizeof(cpx<T>) / 16;  // 16-byte chunks per plane
+    static constexpr int CPF = R2 * N * (int)sizeof(T) / 16;   // 16-byte chunks per input
+};
+
+constexpr int A2P_BLOCKS = 3;  // resident blocks per SM of the persistent axis-2 pass
+
+template <class T, int N>
+__global__ void __launch_bounds__(FAST_THREADS, A2P_BLOCKS) k_fast_axis2p(const __grid_constant__ PassParams<T> pp, int ntiles) {
+    using G = A2Geom<T, N>;
+    constexpr int E = G::E, TPL = G::TPL, TL = G::TL, R2 = G::R2, NH = G::NH, PH = G::PH, SP = G::SP;
+    static_assert(FAST_THREADS % R2 == 0, "rows of a tile must tile the threads");
+    constexpr int KS = FAST_THREADS / R2;
+    static_assert(TL * SIdx<T, N, 1>::LP <= G::SS, "an exchange tile must fit a stage buffer");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* const stage0 = (cpx<T>*)smem_raw;  // buffers stage0 + sb * SS
+    cpx<T>* const H = stage0 + 2 * G::SS;      // HS elements: forward H, or the inverse's b0
+    cpx<T>* const b1 = H + G::HS;
+    const cpx<T>* tw = (const cpx<T>*)pp.ax.tw;
+    const int rows = pp.n0 * pp.n1;
+    const int nb2 = pp.nb2;
+    const int nitems = ntiles * pp.njobs;
+    const bool inv = pp.sign > 0;
+    const int c = threadIdx.x / TPL, t = threadIdx.x % TPL;
+    const int srow = threadIdx.x % R2, sk = threadIdx.x / R2;
+
+    auto split = [&](int w, int& jw, int& tile) {
+        jw = (int)pp.fd_tiles.div((unsigned)w);
+        tile = w - jw * ntiles;
+    };
+    auto issue = [&](int w, int q, int sb) {
+        if (w < nitems) {
+            int jw, tl;
+            split(w, jw, tl);
+            const PassJobT<T>& jb = pp.jobs[jw];
+            const int r0 = tl * R2;
+            cpx<T>* dst = stage0 + sb * G::SS;
+            if (inv) {
+                const cpx<T>* src = (const cpx<T>*)jb.in[0] + r0;
+                for (int i = threadIdx.x; i < nb2 * G::CPK; i += FAST_THREADS) {
+                    const int k = i / G::CPK, ch = i % G::CPK;
+                    cp_async16((char*)(dst + k * SP) + 16 * ch, (const char*)(src + k * rows) + 16 * ch);
+                }
+            } else {
+                const char* src = (const char*)((const T*)jb.in[q] + r0 * N);
+                for (int i = threadIdx.x; i < G::CPF; i += FAST_THREADS)
+                    cp_async16((char*)dst + 16 * i, src + 16 * i);
+            }
+        }
+        cp_async_commit();
+    };
+    // units: one per item (inverse) or one per input of the item's job (forward)
+    auto advance = [&](int& ww, int& qq) {
+        if (inv || ++qq >= pp.jobs[pp.fd_tiles.div((unsigned)ww)].nin) {
+            qq = 0;
+            ww += gridDim.x;
+        }
+    };
+    int w = blockIdx.x, q = 0, sb = 0;
+    int nw = w, nq = 0;
+    if (w < nitems) {
+        issue(nw, nq, 0);
+        advance(nw, nq);
+    }
+    cpx<T> x[E];
+    while (w < nitems) {
+        if (nw < nitems) issue(nw, nq, sb ^ 1);
+        else cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        int jw, tl;
+        split(w, jw, tl);
+        const PassJobT<T>& job = pp.jobs[jw];
+        const int r0 = tl * R2;
+        cpx<T>* const S = stage0 + sb * G::SS;
+        // first exchange tile: the inverse reads its staged planes for every
+        // output, so it uses the H region (unused by the inverse); the forward
+        // reads its stage buffer into registers before transforming, so the
+        // buffer itself serves
+        cpx<T>* const b0 = inv ? H : S;
+        if (inv) {
+            const T c0 = job.isym[0].scale;
+            for (int o = 0; o < job.nout; ++o) {
+                const SymT<T> sy = job.osym[o];
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int k = t + TPL * m;
+                    const bool lo = k < NH;
+                    const int kk = lo ? k : N - k;
+                    cpx<T> a = mk((T)0, (T)0), b = mk((T)0, (T)0);
+                    if (kk < nb2) {  // planes above the band are zero (not staged)
+                        const cpx<T>* pr = S + kk * SP + 2 * c;
+                        a = c0 * pr[0];
+                        b = c0 * pr[1];
+                    }
+                    const cpx<T> sc = sym_coef(sy, pp.tabs, 0, 0, kk);
+                    a = sym_mul(sc, a);
+                    b = sym_mul(sc, b);
+                    if (kk == 0 || kk == N / 2) {
+                        a.y = 0;
+                        b.y = 0;
+                    }
+                    if (!lo) {
+                        a = cj(a);
+                        b = cj(b);
+                    }
+                    x[m] = mk(a.x - b.y, a.y + b.x);
+                }
+                fast_fft<T, N, 1>(x, b0, b1, c, t, tw, +1);
+                T* oa = (T*)job.out[o] + ((r0 + 2 * c) * N + t);  // row pair (2c, 2c + 1)
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    oa[TPL * m] = x[m].x;
+                    oa[N + TPL * m] = x[m].y;
+                }
+            }
+        } else {
+            const T* Sr = (const T*)S + (2 * c) * N + t;  // row pair (2c, 2c + 1) of the tile
+#pragma unroll
+            for (int m = 0; m < E; ++m) x[m] = mk(Sr[TPL * m], Sr[N + TPL * m]);
+            fast_fft<T, N, 1>(x, b0, b1, c, t, tw, -1);
+            // stage the packed spectrum to pair Z_k with Z_{N-k}
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; ++m) b0[SIdx<T, N, 1>::at(c, t + TPL * m)] = x[m];
+            __syncthreads();
+            const SymT<T> sy = job.isym[q];
+            for (int k = t; k < nb2; k += TPL) {
+                const cpx<T> zk = b0[SIdx<T, N, 1>::at(c, k)];
+                const cpx<T> zn = cj(b0[SIdx<T, N, 1>::at(c, k == 0 ? 0 : N - k)]);
+                const cpx<T> sc = sym_coef(sy, pp.tabs, 0, 0, k);
+                const cpx<T> sa = sym_mul(sc, (T)0.5 * (zk + zn));
+                const cpx<T> sbv = sym_mul(sc, rot((T)0.5 * (zk - zn), -1));
+                cpx<T>* ha = &H[(2 * c) * PH + k];
+                cpx<T>* hb = &H[(2 * c + 1) * PH + k];
+                *ha = q == 0 ? sa : *ha + sa;
+                *hb = q == 0 ? sbv : *hb + sbv;
+            }
+            if (q == job.nin - 1) {
+                __syncthreads();
+                cpx<T>* dst = (cpx<T>*)job.out[0] + (r0 + srow);
+                for (int k = sk; k < nb2; k += KS) dst[k * rows] = H[srow * PH + k];
+            }
+        }
+        __syncthreads();  // the stage buffer and H may now be refilled
+        w = nw;
+        q = nq;
+        if (nw < nitems) advance(nw, nq);
+        sb ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+template <class T, int N> constexpr size_t fast_axis2p_smem() {
+    using G = A2Geom<T, N>;
+    return ((size_t)2 * G::SS + (size_t)G::HS + (size_t)G::XT) * sizeof(cpx<T>);
+}
+
 template <class T, int N> constexpr size_t fast_c2c_smem(int axis) {
     return ((size_t)2 * C2CGeom<T, N, 1>::TILE +
             (size_t)2 * (FAST_THREADS / (N / FastPlan<N>::E)) * (axis == 1 ? SIdx<T, N, 1>::LP : SIdx<T, N, 0>::LP)) *
