@@ -506,6 +506,62 @@ def test_incremental_state_equation_agrees_with_jacobi_field_route():
     assert l32 < 0.05 and l32 < 0.65 * l16, (l16, l32)
 
 
+@pytest.mark.parametrize("kind", ["cubic", "linear"])
+def test_interp_transpose_and_coordinate_derivative(kind):
+    """The scatter interp_T is the exact transpose of interp (dot test), and
+    interp_grad is the derivative of interp with respect to the coordinates
+    (central differences)."""
+    n = (7, 6, 9)
+    r = synth.rng_for(120)
+    f = r.standard_normal((2,) + n)
+    pts = r.uniform(-3.0, 12.0, (3, 5, 4, 6))
+    y = r.standard_normal((2, 5, 4, 6))
+    lhs = float(np.sum(O.interp(f, pts, kind) * y))
+    rhs = float(np.sum(f * O.interp_T(y, pts, n, kind)))
+    assert abs(lhs - rhs) < 1e-12 * (abs(lhs) + abs(rhs))
+    G = O.interp_grad(f, pts, kind)
+    for a in range(3):
+        e = np.zeros((3, 1, 1, 1))
+        e[a] = 1e-6
+        fd = (O.interp(f, pts + e, kind) - O.interp(f, pts - e, kind)) / 2e-6
+        assert rel(G[a], fd) < 1e-7
+
+
+@pytest.mark.parametrize("kind", ["cubic", "linear"])
+def test_exact_discrete_gradient_matches_finite_differences(kind):
+    """With the semi-Lagrangian steps and the warp transposed exactly, the
+    gradient is the derivative of the discrete energy: central differences in
+    random (rough) directions agree to 1e-7 (the Jacobi-field gradient of
+    Sec. 3 differs from them by its linearisation gap, order one on this
+    coarse grid)."""
+    n, nt = (10, 12, 8), 3
+    g = O.Grid(n, alpha=0.02)
+    I0, vt = synth.blob_pair_inputs(n, 5, kmax=2, max_disp_vox=1.5)
+    I0 = synth.spectral_gaussian_smooth(I0, 0.8)
+    I1 = O.shoot(g, vt, nt, I0, kind).m1 + 0.01 * synth.rng_for(3).standard_normal(n)
+    p = O.Params(alpha=0.02, nt=nt, interp=kind)
+    v0 = 0.6 * vt + 0.05 * synth.band_limited_field(n, synth.rng_for(4), 2.0, 3) * g.h[0]
+    ge, E = O.gradient_exact(g, p, v0, I0, I1)
+    assert abs(E - O.energy(g, p, v0, I0, I1)[0]) < 1e-15 * E
+    r = synth.rng_for(9)
+    for _ in range(4):
+        d = r.standard_normal((3,) + n) * g.h[0]
+        eps = 1e-5
+        fd = (O.energy(g, p, v0 + eps * d, I0, I1)[0] - O.energy(g, p, v0 - eps * d, I0, I1)[0]) / (2 * eps)
+        assert abs(g.dot(ge, d) - fd) < 1e-7 * abs(fd)
+    # closed form at v0 = 0: the map moves by -P delta, and the warp's
+    # derivative at the grid nodes is the interpolant's own finite difference
+    # (central for Catmull-Rom, forward for trilinear), so
+    # g = P(-2 (I0 - I1) D_h I0) with that difference in place of grad
+    zero = np.zeros((3,) + n)
+    if kind == "cubic":
+        Dh = [(np.roll(I0, -1, a) - np.roll(I0, 1, a)) / (2 * g.h[a]) for a in range(3)]
+    else:
+        Dh = [(np.roll(I0, -1, a) - I0) / g.h[a] for a in range(3)]
+    want = g.P(-2.0 * (I0 - I1)[None] * np.stack(Dh))
+    assert rel(O.gradient_exact(g, p, zero, I0, I1)[0], want) < 1e-12
+
+
 @pytest.mark.parametrize("n", [(20, 12, 18), (12, 10, 15), (128, 128, 128), (256, 300, 256)])
 def test_dealias_band_count_closed_form(n):
     """P keeps exactly (2K0+1)(2K1+1)(K2+1) half-spectrum modes, K_a = (n_a-1)//3,
