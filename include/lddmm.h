@@ -62,6 +62,7 @@ enum { LDDMM_F64 = 0, LDDMM_F32 = 1, LDDMM_BF16 = 2 };          /* number types 
 enum { LDDMM_INTERP_CUBIC = 0, LDDMM_INTERP_LINEAR = 1 };       /* SL interpolant */
 enum { LDDMM_SPACE_V = 0, LDDMM_SPACE_L2 = 1 };                 /* metric of g, Hv */
 enum { LDDMM_OPT_GN = 0, LDDMM_OPT_GD = 1 };                     /* lddmm_register  */
+enum { LDDMM_GRAD_JACOBI = 0, LDDMM_GRAD_DISCRETE = 1 };         /* gradient_mode   */
 
 typedef struct {
     int n[3];        /* grid points per axis                                  */
@@ -94,6 +95,15 @@ typedef struct {
                             (n_a - 1)/3 kept; 0: unfiltered products           */
     int optimizer;       /* LDDMM_OPT_GN (default): Gauss-Newton-Krylov;
                             LDDMM_OPT_GD: gradient descent in V (Sec. 2.2) */
+    int gradient_mode;   /* LDDMM_GRAD_JACOBI (default): the reduced gradient of
+                            Sec. 3 (adjoint Jacobi sweep from the final-time
+                            source, delta m1 = -grad m1 . xi1);
+                            LDDMM_GRAD_DISCRETE: the exact gradient of the
+                            discrete energy, through the transposes of the
+                            semi-Lagrangian map steps and of the warp (needs
+                            state_dtype = compute_dtype and checkpoint_every
+                            <= 1; keeps every map u_k, 6 (nt + 1) more real
+                            fields).  The Gauss-Newton Hv is the same in both. */
 } lddmm_params;
 
 #define LDDMM_TRACE_MAX 64

@@ -19,6 +19,7 @@ LDDMM_F64, LDDMM_F32, LDDMM_BF16 = 0, 1, 2
 LDDMM_INTERP_CUBIC, LDDMM_INTERP_LINEAR = 0, 1
 LDDMM_SPACE_V, LDDMM_SPACE_L2 = 0, 1
 LDDMM_OPT_GN, LDDMM_OPT_GD = 0, 1
+LDDMM_GRAD_JACOBI, LDDMM_GRAD_DISCRETE = 0, 1
 LDDMM_TRACE_MAX = 64
 
 STATUS = {
@@ -41,7 +42,7 @@ class lddmm_params(ctypes.Structure):
         ("compute_dtype", ctypes.c_int), ("state_dtype", ctypes.c_int),
         ("checkpoint_every", ctypes.c_int), ("gn_maxit", ctypes.c_int), ("pcg_maxit", ctypes.c_int),
         ("pcg_rtol", ctypes.c_double), ("armijo_c1", ctypes.c_double), ("ls_maxit", ctypes.c_int),
-        ("dealias", ctypes.c_int), ("optimizer", ctypes.c_int),
+        ("dealias", ctypes.c_int), ("optimizer", ctypes.c_int), ("gradient_mode", ctypes.c_int),
     ]
 
 

@@ -25,6 +25,10 @@ static bool params_ok(const lddmm_params* p) {
     if (p->gn_maxit < 0 || p->pcg_maxit < 0 || p->ls_maxit < 1) return false;
     if (p->dealias != 0 && p->dealias != 1) return false;
     if (p->optimizer != LDDMM_OPT_GN && p->optimizer != LDDMM_OPT_GD) return false;
+    if (p->gradient_mode != LDDMM_GRAD_JACOBI && p->gradient_mode != LDDMM_GRAD_DISCRETE) return false;
+    // the transposed map steps read the stored stage velocities in the compute type
+    if (p->gradient_mode == LDDMM_GRAD_DISCRETE && (p->state_dtype != p->compute_dtype || p->checkpoint_every > 1))
+        return false;
     return true;
 }
 
@@ -48,6 +52,7 @@ void lddmm_default_params(lddmm_params* p) {
     p->ls_maxit = 10;
     p->dealias = 1;
     p->optimizer = LDDMM_OPT_GN;
+    p->gradient_mode = LDDMM_GRAD_JACOBI;
 }
 
 size_t lddmm_workspace_bytes(const lddmm_grid* g, const lddmm_params* p) {

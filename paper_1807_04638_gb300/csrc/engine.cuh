@@ -115,6 +115,8 @@ inline Layout layout_for(const Dims& d, const lddmm_params* p, size_t tsize) {
     const bool ckpt = cpe < p->nt;
     const int nseg = (p->nt + cpe - 1) / cpe;
     L.real_fields = 6 + 6 + RSCR + 1 + 3 + 1 + 3 + 21 + 6;
+    // exact discrete gradient: every map u_k, every dE/dv_k, two dE/du buffers
+    if (p->gradient_mode == LDDMM_GRAD_DISCRETE) L.real_fields += (size_t)6 * (p->nt + 1) + 6;
     if (ckpt) L.spec_fields += (size_t)3 * nseg;  // spectral v at the checkpoints
     size_t b = L.spec_fields * d.NS * 2 * tsize + L.real_fields * d.N * tsize;
     // stored time states: every stage, or one segment of checkpoint_every steps
@@ -316,6 +318,9 @@ class Engine : public EngineBase {
     bool ckpt = false;
     C* cps = nullptr;
     T *vfin, *ubuf[2], *rs, *m1, *gm1, *rbuf, *lv0, *vss[2] = {nullptr, nullptr};
+    // exact discrete gradient: maps u_k (k = 0..nt), dE/dv_k, dE/du ping-pong
+    T *ustore = nullptr, *vbar = nullptr, *ubar[2] = {nullptr, nullptr};
+    bool exact_grad = false;
     T *px, *pr, *pz, *pp, *pq, *pg, *pvt;
     double *partial, *dres, *hres = nullptr;
     FFTAxis ax[3];
@@ -466,6 +471,12 @@ class Engine : public EngineBase {
         if (ckpt) cps = carve<C>((size_t)3 * nseg * d.NS);
         vfin = carve<T>(6 * d.N);
         for (int i = 0; i < 2; ++i) ubuf[i] = carve<T>(3 * d.N);
+        exact_grad = prm.gradient_mode == LDDMM_GRAD_DISCRETE;
+        if (exact_grad) {
+            ustore = carve<T>((size_t)3 * (prm.nt + 1) * d.N);
+            vbar = carve<T>((size_t)3 * (prm.nt + 1) * d.N);
+            for (int i = 0; i < 2; ++i) ubar[i] = carve<T>(3 * d.N);
+        }
         rs = carve<T>((size_t)RSCR * d.N);
         m1 = carve<T>(d.N);
         gm1 = carve<T>(3 * d.N);
@@ -583,6 +594,9 @@ class Engine : public EngineBase {
         return (size_t)l * 24 * d.N;
     }
     T* state(int s) const { return (T*)states + sofs(s); }
+    // the map u_k: every step kept for the exact discrete gradient, else two
+    // ping-pong buffers
+    T* ubuf_at(int k) const { return exact_grad ? ustore + (size_t)3 * k * d.N : ubuf[k % 2]; }
     __nv_bfloat16* state_bf(int s) const { return (__nv_bfloat16*)states + sofs(s); }
     double state_elem() const { return bf16 ? 2.0 : (double)sizeof(T); }
     double dt() const { return 1.0 / prm.nt; }
@@ -1014,7 +1028,7 @@ class Engine : public EngineBase {
         if (kinetic) dot_async(S1 + 12 * d.N, S1, 3 * d.N, k, d.cell);
         if (transport && k >= 1) {
             PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
-            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vss[(k - 1) % 2], S1, ubuf[(k - 1) % 2], ubuf[k % 2],
+            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vss[(k - 1) % 2], S1, ubuf_at(k - 1), ubuf_at(k),
                                                              (T)dt_, ih0, ih1, ih2, cubic, d.N);
         }
         {
@@ -1072,7 +1086,7 @@ class Engine : public EngineBase {
         const int cubic = prm.interp == LDDMM_INTERP_CUBIC;
         fwd_vec(v0, v0full);
         mask_copy(v0full, v0hat);
-        cudaMemsetAsync(ubuf[0], 0, 3 * d.N * sizeof(T), st);
+        cudaMemsetAsync(ubuf_at(0), 0, 3 * d.N * sizeof(T), st);
         for (int k = 0; k < nt; ++k) {
             C* cur = k == 0 ? v0hat : vhat[k % 2];
             C* nxt = vhat[(k + 1) % 2];
@@ -1101,11 +1115,11 @@ class Engine : public EngineBase {
         if (kinetic) dot_async(vfin + 3 * d.N, vfin, 3 * d.N, nt, d.cell);
         {
             PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
-            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vss[(nt - 1) % 2], vfin, ubuf[(nt - 1) % 2],
-                                                             ubuf[nt % 2], (T)dt_, ih0, ih1, ih2, cubic, d.N);
+            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vss[(nt - 1) % 2], vfin, ubuf_at(nt - 1),
+                                                             ubuf_at(nt), (T)dt_, ih0, ih1, ih2, cubic, d.N);
         }
     }
-    T* u1() const { return ubuf[prm.nt % 2]; }
+    T* u1() const { return ubuf_at(prm.nt); }
 
     void warp_and_grad(const T* I0) {
         const GridI gi{d.n0, d.n1, d.n2};
@@ -1200,8 +1214,10 @@ class Engine : public EngineBase {
         }
     }
 
-    // adjoint: from adj[0] = (ybar_eta, ybar_xi) at t = 1; result in adj[nt % 2]
-    void adjoint_sweep() {
+    // adjoint: from adj[0] = (ybar_eta, ybar_xi) at t = 1; result in adj[nt % 2].
+    // eta_src (nullable): real cotangents on eta_k, k = 0..nt (3 fields each),
+    // added to ybar_eta after the transposed step k (exact discrete gradient)
+    void adjoint_sweep(const T* eta_src = nullptr) {
         const double dt_ = dt();
         T* Y = rs;              // 6 fields
         T* G = rs + 6 * d.N;    // 36 fields
@@ -1264,6 +1280,7 @@ class Engine : public EngineBase {
                         oe.bases.push_back({ae + c * d.NS, 0.5 * dt_});
                         oe.bases.push_back({cx + c * d.NS, 0.5 * dt_});
                         oe.bases.push_back({axp + c * d.NS, 0.5 * dt_ * dt_});
+                        if (eta_src) oe.terms.push_back({eta_src + ((size_t)3 * k + c) * d.N, sym(1.0, 0, -1)});
                         ox.out = nxt + (3 + c) * d.NS;
                         ox.bases.push_back({cx + c * d.NS, 1.0});
                         ox.bases.push_back({axp + c * d.NS, 0.5 * dt_});
@@ -1297,6 +1314,35 @@ class Engine : public EngineBase {
         inv_vec(tmp, out);
     }
 
+    // Exact discrete gradient, transport part: dE_data/dv_k (k = 0..nt) into
+    // vbar through the transposes of the warp and of the map steps, backwards
+    // from t = 1 (needs the maps u_k of the last shoot and m1).
+    void exact_data_cotangents(const T* I0, const T* I1) {
+        const GridI gi{d.n0, d.n1, d.n2};
+        const T ih0 = (T)(1.0 / d.h[0]), ih1 = (T)(1.0 / d.h[1]), ih2 = (T)(1.0 / d.h[2]);
+        const int cubic = prm.interp == LDDMM_INTERP_CUBIC;
+        const int nt = prm.nt;
+        cudaMemsetAsync(vbar, 0, (size_t)3 * (nt + 1) * d.N * sizeof(T), st);
+        {
+            PScope ps_(this, KC_WARP, 8.0 * d.N * sizeof(T));
+            k_warp_adj<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, I0, u1(), m1, I1, ubar[0], ih0, ih1, ih2, cubic,
+                                                              d.N);
+        }
+        int cu = 0;
+        for (int k = nt - 1; k >= 0; --k) {
+            cudaMemsetAsync(ubar[1 - cu], 0, 3 * d.N * sizeof(T), st);
+            const T* vk = state(2 * k);                            // stage-1 velocity v_k
+            const T* vk1 = k + 1 == nt ? vfin : state(2 * (k + 1));  // v_{k+1}
+            {
+                PScope ps_(this, KC_SL, 24.0 * d.N * sizeof(T));
+                k_sl_adj<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(
+                    gi, vk, vk1, ubuf_at(k), ubar[cu], ubar[1 - cu], vbar + (size_t)3 * k * d.N,
+                    vbar + (size_t)3 * (k + 1) * d.N, (T)dt(), ih0, ih1, ih2, cubic, d.N);
+            }
+            cu = 1 - cu;
+        }
+    }
+
     // gradient internals: E into dres[nt+1..nt+3]; gradient real in metric `space`
     void gradient_core(const T* v0, const T* I0, const T* I1, T* grad, int space) {
         shoot_core(v0, true);
@@ -1307,13 +1353,21 @@ class Engine : public EngineBase {
         }
         dot_async(rbuf, nullptr, d.N, prm.nt + 2, d.cell);
         reg_async(v0, prm.nt + 1);
-        {
-            PScope ps_(this, KC_MISC, 8.0 * d.N * sizeof(T));
-            k_final_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, gm1, nullptr, rs, 0, d.N);
+        if (exact_grad) {
+            exact_data_cotangents(I0, I1);
+            // eta block from dE/dv_nt, xi block zero; dE/dv_k enter along the way
+            fwd_vec(vbar + (size_t)3 * prm.nt * d.N, adj[0], 1.0, 0, true);
+            cudaMemsetAsync(adj[0] + 3 * d.NS, 0, 3 * d.NS * sizeof(C), st);
+            adjoint_sweep(vbar);
+        } else {
+            {
+                PScope ps_(this, KC_MISC, 8.0 * d.N * sizeof(T));
+                k_final_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(m1, I1, gm1, nullptr, rs, 0, d.N);
+            }
+            fwd_vec(rs, adj[0] + 3 * d.NS, 1.0, 0, true);
+            cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
+            adjoint_sweep();
         }
-        fwd_vec(rs, adj[0] + 3 * d.NS, 1.0, 0, true);
-        cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
-        adjoint_sweep();
         // g_L2 = 2 w L v0 + T^T b ;  V: K g_L2 = 2 w v0 + K T^T b
         const double w2 = 2.0 * prm.weight;
         if (space == LDDMM_SPACE_V)

@@ -247,6 +247,157 @@ __global__ void k_warp(GridI g, const T* __restrict__ img, const T* __restrict__
     }
 }
 
+// ---------------------------------------------------------------- exact adjoint of the transport
+// Interpolation weights w and their coordinate derivatives dw for one point.
+template <class T> __device__ __forceinline__ void cr_dweights(T t, T* dw) {
+    const T t2 = t * t;
+    dw[0] = (T)0.5 * ((T)-3 * t2 + (T)4 * t - (T)1);
+    dw[1] = (T)0.5 * ((T)9 * t2 - (T)10 * t);
+    dw[2] = (T)0.5 * ((T)-9 * t2 + (T)8 * t + (T)1);
+    dw[3] = (T)0.5 * ((T)3 * t2 - (T)2 * t);
+}
+template <class T> struct Taps {
+    int base[3];
+    T w[3][4], dw[3][4];
+    int lo, cnt;
+    __device__ __forceinline__ Taps(int i0, int i1, int i2, const T d[3], int cubic) {
+        const int ii[3] = {i0, i1, i2};
+        lo = cubic ? -1 : 0;
+        cnt = cubic ? 4 : 2;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T fl = floor(d[a]);
+            const T t = d[a] - fl;
+            base[a] = ii[a] + (int)fl;
+            if (cubic) {
+                cr_weights(t, w[a]);
+                cr_dweights(t, dw[a]);
+            } else {
+                w[a][0] = (T)1 - t;
+                w[a][1] = t;
+                dw[a][0] = (T)-1;
+                dw[a][1] = (T)1;
+            }
+        }
+    }
+};
+
+// d/dp_b of the interpolant of NC fields at the point: G[b][c]
+template <class T, int NC>
+__device__ __forceinline__ void interp_grad_at(const T* __restrict__ f, size_t N, GridI g, const Taps<T>& tp,
+                                               T (&G)[3][NC]) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) G[b][c] = 0;
+    for (int a0 = 0; a0 < tp.cnt; ++a0) {
+        const size_t o0 = (size_t)wrapi(tp.base[0] + tp.lo + a0, g.n0) * g.n1;
+        for (int a1 = 0; a1 < tp.cnt; ++a1) {
+            const size_t o1 = (o0 + wrapi(tp.base[1] + tp.lo + a1, g.n1)) * g.n2;
+            for (int a2 = 0; a2 < tp.cnt; ++a2) {
+                const size_t o = o1 + wrapi(tp.base[2] + tp.lo + a2, g.n2);
+                const T g0 = tp.dw[0][a0] * tp.w[1][a1] * tp.w[2][a2];
+                const T g1 = tp.w[0][a0] * tp.dw[1][a1] * tp.w[2][a2];
+                const T g2 = tp.w[0][a0] * tp.w[1][a1] * tp.dw[2][a2];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const T val = __ldg(&f[c * N + o]);
+                    G[0][c] += g0 * val;
+                    G[1][c] += g1 * val;
+                    G[2][c] += g2 * val;
+                }
+            }
+        }
+    }
+}
+
+// Transpose of the interpolation at the point: fb[taps] += w * vals (atomic)
+template <class T, int NC>
+__device__ __forceinline__ void interp_scatter_at(T* fb, size_t N, GridI g, const Taps<T>& tp, const T (&vals)[NC]) {
+    for (int a0 = 0; a0 < tp.cnt; ++a0) {
+        const size_t o0 = (size_t)wrapi(tp.base[0] + tp.lo + a0, g.n0) * g.n1;
+        for (int a1 = 0; a1 < tp.cnt; ++a1) {
+            const size_t o1 = (o0 + wrapi(tp.base[1] + tp.lo + a1, g.n1)) * g.n2;
+            const T w01 = tp.w[0][a0] * tp.w[1][a1];
+            for (int a2 = 0; a2 < tp.cnt; ++a2) {
+                const size_t o = o1 + wrapi(tp.base[2] + tp.lo + a2, g.n2);
+                const T ww = w01 * tp.w[2][a2];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) atomicAdd(&fb[c * N + o], ww * vals[c]);
+            }
+        }
+    }
+}
+
+// Cotangent of the final warp m1 = I0(x + u/h) with respect to u, for
+// E_data = ||m1 - I1||^2:  ub(x) = 2 (m1 - I1)(x) dI0/dp(x + u/h) / h.
+template <class T>
+__global__ void k_warp_adj(GridI g, const T* __restrict__ img, const T* __restrict__ u, const T* __restrict__ m1,
+                           const T* __restrict__ I1, T* __restrict__ ub, T ih0, T ih1, T ih2, int cubic, size_t N) {
+    const T ih[3] = {ih0, ih1, ih2};
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        const int i2 = (int)(x % g.n2);
+        const int i1 = (int)((x / g.n2) % g.n1);
+        const int i0 = (int)(x / ((size_t)g.n2 * g.n1));
+        T d[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[c] = u[c * N + x] * ih[c];
+        const Taps<T> tp(i0, i1, i2, d, cubic);
+        T G[3][1];
+        interp_grad_at<T, 1>(img, N, g, tp, G);
+        const T r2 = (T)2 * (m1[x] - I1[x]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) ub[b * N + x] = r2 * G[b][0] * ih[b];
+    }
+}
+
+// Transpose of one map step (k_sl_step) u_{k+1} = disp + u_k(X),
+// X = x + disp/h, disp = -dt/2 (v1 + v0(p1)), p1 = x - dt v1/h:
+// from ub1 = dE/du_{k+1}, scatter dE/du_k into ub0 and the v0(p1) part of
+// dE/dv_k into vb0 (both atomic), and add the v1 part of dE/dv_{k+1} to vb1.
+template <class T>
+__global__ void k_sl_adj(GridI g, const T* __restrict__ v0, const T* __restrict__ v1, const T* __restrict__ u0,
+                         const T* __restrict__ ub1, T* ub0, T* vb0, T* __restrict__ vb1, T dt, T ih0, T ih1, T ih2,
+                         int cubic, size_t N) {
+    const T ih[3] = {ih0, ih1, ih2};
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        const int i2 = (int)(x % g.n2);
+        const int i1 = (int)((x / g.n2) % g.n1);
+        const int i0 = (int)(x / ((size_t)g.n2 * g.n1));
+        T w1[3], d1[3], vt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            w1[c] = v1[c * N + x];
+            d1[c] = -dt * w1[c] * ih[c];
+        }
+        interp_at<T, 3>(v0, N, g, i0, i1, i2, d1, cubic, vt);
+        T dX[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dX[c] = (T)-0.5 * dt * (w1[c] + vt[c]) * ih[c];
+        const Taps<T> tX(i0, i1, i2, dX, cubic);
+        T Gu[3][3];
+        interp_grad_at<T, 3>(u0, N, g, tX, Gu);
+        T ub[3], dispb[3], vtb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ub[c] = ub1[c * N + x];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            dispb[b] = ub[b] + ih[b] * (Gu[b][0] * ub[0] + Gu[b][1] * ub[1] + Gu[b][2] * ub[2]);
+            vtb[b] = (T)-0.5 * dt * dispb[b];
+        }
+        interp_scatter_at<T, 3>(ub0, N, g, tX, ub);
+        const Taps<T> t1(i0, i1, i2, d1, cubic);
+        interp_scatter_at<T, 3>(vb0, N, g, t1, vtb);
+        T Gv[3][3];
+        interp_grad_at<T, 3>(v0, N, g, t1, Gv);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const T p1b = Gv[b][0] * vtb[0] + Gv[b][1] * vtb[1] + Gv[b][2] * vtb[2];
+            vb1[b * N + x] += (T)-0.5 * dt * dispb[b] - dt * ih[b] * p1b;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- reductions
 // Deterministic two-phase double reductions: block partials, then one block.
 constexpr int RED_THREADS = 256;

@@ -205,6 +205,59 @@ def test_register_gradient_descent_matches_oracle(pkg):
     assert abs(rep["mse_rel"] - ref.mse_rel) < 1e-9 and abs(rep["gnorm_rel"] - ref.gnorm_rel) < 1e-9
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["cubic", "linear"])
+@pytest.mark.parametrize("n", [(10, 12, 8), (32, 32, 32)])
+def test_gradient_discrete_matches_oracle(pkg, prec, kind, n):
+    """gradient_mode = LDDMM_GRAD_DISCRETE: the exact gradient of the discrete
+    energy (transposed map steps and warp) against the oracle's."""
+    dtype, _ = DT[prec]
+    nt = 3
+    g = O.Grid(n, alpha=0.02)
+    I0, vt = synth.blob_pair_inputs(n, 5, kmax=2, max_disp_vox=1.5)
+    I0 = synth.spectral_gaussian_smooth(I0, 0.8)
+    I1 = O.shoot(g, vt, nt, I0, kind).m1 + 0.01 * synth.rng_for(3).standard_normal(n)
+    p = O.Params(alpha=0.02, nt=nt, interp=kind)
+    v0 = 0.6 * vt + 0.05 * synth.band_limited_field(n, synth.rng_for(4), 2.0, 3) * g.h[0]
+    want, E = O.gradient_exact(g, p, v0, I0, I1)
+    ik = pkg.LDDMM_INTERP_CUBIC if kind == "cubic" else pkg.LDDMM_INTERP_LINEAR
+    prm = params(pkg, prec, alpha=0.02, nt=nt, interp=ik, space=pkg.LDDMM_SPACE_L2,
+                 gradient_mode=pkg.LDDMM_GRAD_DISCRETE)
+    with pkg.Handle(n, prm) as h:
+        grad = h.new_vec()
+        e = h.lddmm_gradient(dev(v0, dtype), dev(I0, dtype), dev(I1, dtype), grad)
+        h.lddmm_synchronize()
+        got = host(grad)
+    tol = 1e-10 if prec == "f64" else 1e-5
+    assert abs(e[0] - E) < tol * E
+    assert rel(got, want) < tol, rel(got, want)
+
+
+def test_gradient_discrete_finite_differences_on_gpu(pkg):
+    """The FP64 GPU exact gradient against central differences of the GPU's own
+    energy in rough random directions."""
+    n, nt = (12, 10, 8), 3
+    g = O.Grid(n, alpha=0.02)
+    I0, vt = synth.blob_pair_inputs(n, 6, kmax=2, max_disp_vox=1.5)
+    I0 = synth.spectral_gaussian_smooth(I0, 0.8)
+    I1 = O.shoot(g, vt, nt, I0).m1
+    v0 = 0.5 * vt
+    prm = params(pkg, "f64", alpha=0.02, nt=nt, space=pkg.LDDMM_SPACE_L2, gradient_mode=pkg.LDDMM_GRAD_DISCRETE)
+    f64 = torch.float64
+    with pkg.Handle(n, prm) as h:
+        grad, scratch = h.new_vec(), h.new_vec()
+        h.lddmm_gradient(dev(v0, f64), dev(I0, f64), dev(I1, f64), grad)
+        gnp = host(grad)
+        r = synth.rng_for(77)
+        for _ in range(3):
+            d = r.standard_normal((3,) + n) * g.h[0]
+            eps = 1e-5
+            ep = h.lddmm_gradient(dev(v0 + eps * d, f64), dev(I0, f64), dev(I1, f64), scratch)[0]
+            em = h.lddmm_gradient(dev(v0 - eps * d, f64), dev(I0, f64), dev(I1, f64), scratch)[0]
+            fd = (ep - em) / (2 * eps)
+            assert abs(g.dot(gnp, d) - fd) < 1e-7 * abs(fd)
+
+
 def test_errors_are_reported(pkg):
     n = (8, 8, 8)
     with pytest.raises(pkg.LddmmError):
