@@ -553,6 +553,27 @@ def finish(args, out, h, v0t, d, I0, I1, stream, dev, rank, P, NG):
         del h64
         torch.cuda.empty_cache()
 
+    # ---- one reduced gradient per mode: Jacobi-field (Sec. 3) and the exact
+    # gradient of the discrete energy (transposed transport)
+    if not args.no_fp64 and rank == 0:
+        gm = {}
+        for name, mode in (("jacobi", pkg.LDDMM_GRAD_JACOBI), ("discrete", pkg.LDDMM_GRAD_DISCRETE)):
+            prmg = pkg.default_params(**{f: getattr(prm, f) for f, _ in prm._fields_})
+            prmg.gradient_mode = mode
+            hg = pkg.Handle(NG, prmg, stream=stream, device=dev.index)
+            vg, gg = torch.tensor(0.5 * v0t, dtype=f32, device=dev), hg.new_vec()
+            hg.lddmm_gradient(vg, I0, I1, gg, energy=False)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                hg.lddmm_gradient(vg, I0, I1, gg, energy=False)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            gm[name + "_ms"] = round(e0.elapsed_time(e1) / 3, 3)
+            hg.close()
+        out["gradient"] = gm
+
     # ---- cuFFT cross-check of the K-apply: the library FFT (torch.fft) timed
     # beside the hand-written passes on the same 3-component 128^3 FP32 field
     if not args.no_fp64 and rank == 0:

@@ -1325,8 +1325,12 @@ class Engine : public EngineBase {
         cudaMemsetAsync(vbar, 0, (size_t)3 * (nt + 1) * d.N * sizeof(T), st);
         {
             PScope ps_(this, KC_WARP, 8.0 * d.N * sizeof(T));
-            k_warp_adj<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, I0, u1(), m1, I1, ubar[0], ih0, ih1, ih2, cubic,
-                                                              d.N);
+            if (cubic)
+                k_warp_adj<T, true><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, I0, u1(), m1, I1, ubar[0], ih0, ih1, ih2,
+                                                                        d.N);
+            else
+                k_warp_adj<T, false><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, I0, u1(), m1, I1, ubar[0], ih0, ih1,
+                                                                         ih2, d.N);
         }
         int cu = 0;
         for (int k = nt - 1; k >= 0; --k) {
@@ -1335,9 +1339,16 @@ class Engine : public EngineBase {
             const T* vk1 = k + 1 == nt ? vfin : state(2 * (k + 1));  // v_{k+1}
             {
                 PScope ps_(this, KC_SL, 24.0 * d.N * sizeof(T));
-                k_sl_adj<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(
-                    gi, vk, vk1, ubuf_at(k), ubar[cu], ubar[1 - cu], vbar + (size_t)3 * k * d.N,
-                    vbar + (size_t)3 * (k + 1) * d.N, (T)dt(), ih0, ih1, ih2, cubic, d.N);
+                T* vb0 = vbar + (size_t)3 * k * d.N;
+                T* vb1 = vbar + (size_t)3 * (k + 1) * d.N;
+                if (cubic)
+                    k_sl_adj<T, true><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vk, vk1, ubuf_at(k), ubar[cu],
+                                                                          ubar[1 - cu], vb0, vb1, (T)dt(), ih0, ih1,
+                                                                          ih2, d.N);
+                else
+                    k_sl_adj<T, false><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vk, vk1, ubuf_at(k), ubar[cu],
+                                                                           ubar[1 - cu], vb0, vb1, (T)dt(), ih0, ih1,
+                                                                           ih2, d.N);
             }
             cu = 1 - cu;
         }

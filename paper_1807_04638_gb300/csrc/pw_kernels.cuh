@@ -256,20 +256,22 @@ template <class T> __device__ __forceinline__ void cr_dweights(T t, T* dw) {
     dw[2] = (T)0.5 * ((T)-9 * t2 + (T)8 * t + (T)1);
     dw[3] = (T)0.5 * ((T)3 * t2 - (T)2 * t);
 }
-template <class T> struct Taps {
+// Taps of one point for the Catmull-Rom (CUBIC) or trilinear interpolant,
+// with the tap count known at compile time (the weight arrays stay in
+// registers).
+template <class T, bool CUBIC> struct Taps {
+    static constexpr int CNT = CUBIC ? 4 : 2;
+    static constexpr int LO = CUBIC ? -1 : 0;
     int base[3];
-    T w[3][4], dw[3][4];
-    int lo, cnt;
-    __device__ __forceinline__ Taps(int i0, int i1, int i2, const T d[3], int cubic) {
+    T w[3][CNT], dw[3][CNT];
+    __device__ __forceinline__ Taps(int i0, int i1, int i2, const T d[3]) {
         const int ii[3] = {i0, i1, i2};
-        lo = cubic ? -1 : 0;
-        cnt = cubic ? 4 : 2;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const T fl = floor(d[a]);
             const T t = d[a] - fl;
             base[a] = ii[a] + (int)fl;
-            if (cubic) {
+            if constexpr (CUBIC) {
                 cr_weights(t, w[a]);
                 cr_dweights(t, dw[a]);
             } else {
@@ -283,19 +285,23 @@ template <class T> struct Taps {
 };
 
 // d/dp_b of the interpolant of NC fields at the point: G[b][c]
-template <class T, int NC>
-__device__ __forceinline__ void interp_grad_at(const T* __restrict__ f, size_t N, GridI g, const Taps<T>& tp,
+template <class T, bool CUBIC, int NC>
+__device__ __forceinline__ void interp_grad_at(const T* __restrict__ f, size_t N, GridI g, const Taps<T, CUBIC>& tp,
                                                T (&G)[3][NC]) {
+    constexpr int CNT = Taps<T, CUBIC>::CNT, LO = Taps<T, CUBIC>::LO;
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int c = 0; c < NC; ++c) G[b][c] = 0;
-    for (int a0 = 0; a0 < tp.cnt; ++a0) {
-        const size_t o0 = (size_t)wrapi(tp.base[0] + tp.lo + a0, g.n0) * g.n1;
-        for (int a1 = 0; a1 < tp.cnt; ++a1) {
-            const size_t o1 = (o0 + wrapi(tp.base[1] + tp.lo + a1, g.n1)) * g.n2;
-            for (int a2 = 0; a2 < tp.cnt; ++a2) {
-                const size_t o = o1 + wrapi(tp.base[2] + tp.lo + a2, g.n2);
+#pragma unroll
+    for (int a0 = 0; a0 < CNT; ++a0) {
+        const size_t o0 = (size_t)wrapi(tp.base[0] + LO + a0, g.n0) * g.n1;
+#pragma unroll
+        for (int a1 = 0; a1 < CNT; ++a1) {
+            const size_t o1 = (o0 + wrapi(tp.base[1] + LO + a1, g.n1)) * g.n2;
+#pragma unroll
+            for (int a2 = 0; a2 < CNT; ++a2) {
+                const size_t o = o1 + wrapi(tp.base[2] + LO + a2, g.n2);
                 const T g0 = tp.dw[0][a0] * tp.w[1][a1] * tp.w[2][a2];
                 const T g1 = tp.w[0][a0] * tp.dw[1][a1] * tp.w[2][a2];
                 const T g2 = tp.w[0][a0] * tp.w[1][a1] * tp.dw[2][a2];
@@ -312,15 +318,20 @@ __device__ __forceinline__ void interp_grad_at(const T* __restrict__ f, size_t N
 }
 
 // Transpose of the interpolation at the point: fb[taps] += w * vals (atomic)
-template <class T, int NC>
-__device__ __forceinline__ void interp_scatter_at(T* fb, size_t N, GridI g, const Taps<T>& tp, const T (&vals)[NC]) {
-    for (int a0 = 0; a0 < tp.cnt; ++a0) {
-        const size_t o0 = (size_t)wrapi(tp.base[0] + tp.lo + a0, g.n0) * g.n1;
-        for (int a1 = 0; a1 < tp.cnt; ++a1) {
-            const size_t o1 = (o0 + wrapi(tp.base[1] + tp.lo + a1, g.n1)) * g.n2;
+template <class T, bool CUBIC, int NC>
+__device__ __forceinline__ void interp_scatter_at(T* fb, size_t N, GridI g, const Taps<T, CUBIC>& tp,
+                                                  const T (&vals)[NC]) {
+    constexpr int CNT = Taps<T, CUBIC>::CNT, LO = Taps<T, CUBIC>::LO;
+#pragma unroll
+    for (int a0 = 0; a0 < CNT; ++a0) {
+        const size_t o0 = (size_t)wrapi(tp.base[0] + LO + a0, g.n0) * g.n1;
+#pragma unroll
+        for (int a1 = 0; a1 < CNT; ++a1) {
+            const size_t o1 = (o0 + wrapi(tp.base[1] + LO + a1, g.n1)) * g.n2;
             const T w01 = tp.w[0][a0] * tp.w[1][a1];
-            for (int a2 = 0; a2 < tp.cnt; ++a2) {
-                const size_t o = o1 + wrapi(tp.base[2] + tp.lo + a2, g.n2);
+#pragma unroll
+            for (int a2 = 0; a2 < CNT; ++a2) {
+                const size_t o = o1 + wrapi(tp.base[2] + LO + a2, g.n2);
                 const T ww = w01 * tp.w[2][a2];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) atomicAdd(&fb[c * N + o], ww * vals[c]);
@@ -331,9 +342,9 @@ __device__ __forceinline__ void interp_scatter_at(T* fb, size_t N, GridI g, cons
 
 // Cotangent of the final warp m1 = I0(x + u/h) with respect to u, for
 // E_data = ||m1 - I1||^2:  ub(x) = 2 (m1 - I1)(x) dI0/dp(x + u/h) / h.
-template <class T>
+template <class T, bool CUBIC>
 __global__ void k_warp_adj(GridI g, const T* __restrict__ img, const T* __restrict__ u, const T* __restrict__ m1,
-                           const T* __restrict__ I1, T* __restrict__ ub, T ih0, T ih1, T ih2, int cubic, size_t N) {
+                           const T* __restrict__ I1, T* __restrict__ ub, T ih0, T ih1, T ih2, size_t N) {
     const T ih[3] = {ih0, ih1, ih2};
     for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
         const int i2 = (int)(x % g.n2);
@@ -342,9 +353,9 @@ __global__ void k_warp_adj(GridI g, const T* __restrict__ img, const T* __restri
         T d[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) d[c] = u[c * N + x] * ih[c];
-        const Taps<T> tp(i0, i1, i2, d, cubic);
+        const Taps<T, CUBIC> tp(i0, i1, i2, d);
         T G[3][1];
-        interp_grad_at<T, 1>(img, N, g, tp, G);
+        interp_grad_at<T, CUBIC, 1>(img, N, g, tp, G);
         const T r2 = (T)2 * (m1[x] - I1[x]);
 #pragma unroll
         for (int b = 0; b < 3; ++b) ub[b * N + x] = r2 * G[b][0] * ih[b];
@@ -355,10 +366,10 @@ __global__ void k_warp_adj(GridI g, const T* __restrict__ img, const T* __restri
 // X = x + disp/h, disp = -dt/2 (v1 + v0(p1)), p1 = x - dt v1/h:
 // from ub1 = dE/du_{k+1}, scatter dE/du_k into ub0 and the v0(p1) part of
 // dE/dv_k into vb0 (both atomic), and add the v1 part of dE/dv_{k+1} to vb1.
-template <class T>
+template <class T, bool CUBIC>
 __global__ void k_sl_adj(GridI g, const T* __restrict__ v0, const T* __restrict__ v1, const T* __restrict__ u0,
                          const T* __restrict__ ub1, T* ub0, T* vb0, T* __restrict__ vb1, T dt, T ih0, T ih1, T ih2,
-                         int cubic, size_t N) {
+                         size_t N) {
     const T ih[3] = {ih0, ih1, ih2};
     for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
         const int i2 = (int)(x % g.n2);
@@ -370,13 +381,13 @@ __global__ void k_sl_adj(GridI g, const T* __restrict__ v0, const T* __restrict_
             w1[c] = v1[c * N + x];
             d1[c] = -dt * w1[c] * ih[c];
         }
-        interp_at<T, 3>(v0, N, g, i0, i1, i2, d1, cubic, vt);
+        interp_at<T, 3>(v0, N, g, i0, i1, i2, d1, CUBIC ? 1 : 0, vt);
         T dX[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) dX[c] = (T)-0.5 * dt * (w1[c] + vt[c]) * ih[c];
-        const Taps<T> tX(i0, i1, i2, dX, cubic);
+        const Taps<T, CUBIC> tX(i0, i1, i2, dX);
         T Gu[3][3];
-        interp_grad_at<T, 3>(u0, N, g, tX, Gu);
+        interp_grad_at<T, CUBIC, 3>(u0, N, g, tX, Gu);
         T ub[3], dispb[3], vtb[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) ub[c] = ub1[c * N + x];
@@ -385,11 +396,11 @@ __global__ void k_sl_adj(GridI g, const T* __restrict__ v0, const T* __restrict_
             dispb[b] = ub[b] + ih[b] * (Gu[b][0] * ub[0] + Gu[b][1] * ub[1] + Gu[b][2] * ub[2]);
             vtb[b] = (T)-0.5 * dt * dispb[b];
         }
-        interp_scatter_at<T, 3>(ub0, N, g, tX, ub);
-        const Taps<T> t1(i0, i1, i2, d1, cubic);
-        interp_scatter_at<T, 3>(vb0, N, g, t1, vtb);
+        interp_scatter_at<T, CUBIC, 3>(ub0, N, g, tX, ub);
+        const Taps<T, CUBIC> t1(i0, i1, i2, d1);
+        interp_scatter_at<T, CUBIC, 3>(vb0, N, g, t1, vtb);
         T Gv[3][3];
-        interp_grad_at<T, 3>(v0, N, g, t1, Gv);
+        interp_grad_at<T, CUBIC, 3>(v0, N, g, t1, Gv);
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             const T p1b = Gv[b][0] * vtb[0] + Gv[b][1] * vtb[1] + Gv[b][2] * vtb[2];
