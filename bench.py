@@ -12,8 +12,9 @@ the dominant kernel class, and the FP64 CPU oracle timed on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
-With N > 1 (torchrun) every rank runs an independent replica (the path does
-not shard) and value is the sum over ranks.
+With N > 1 (torchrun) every rank runs an independent replica (one
+registration does not shard without an all-to-all transpose per FFT pass),
+and value is the Hv of all ranks divided by the slowest rank's time.
 """
 from __future__ import annotations
 
