@@ -505,7 +505,7 @@ def jacobian_det(g: Grid, u):
 
 
 def register(g: Grid, p: Params, I0, I1, v0=None, gn_maxit=5, pcg_maxit=10, pcg_rtol=0.1,
-             c1=1e-4, ls_maxit=10, replay=None):
+             c1=1e-4, ls_maxit=10, replay=None, exact_gradient=False):
     """Inexact Gauss-Newton-Krylov registration in the space of initial
     velocities.  Update v0 <- v0 + eps dv0 with H dv0 = -g (the descent sign;
     the paper writes the update with the opposite sign convention on dv0),
@@ -513,6 +513,9 @@ def register(g: Grid, p: Params, I0, I1, v0=None, gn_maxit=5, pcg_maxit=10, pcg_
 
     ``replay`` = list of (pcg_iterations, eps) per GN iteration forces the
     decisions (used to compare trajectories computed at another precision).
+    ``exact_gradient`` uses the gradient of the discrete energy
+    (``gradient_exact``) in place of the Jacobi-field gradient; the
+    Gauss-Newton Hessian is the same.
     """
     v = np.zeros((3,) + g.n) if v0 is None else np.array(v0, dtype=np.float64)
     energies, iters, steps = [], [], []
@@ -520,6 +523,8 @@ def register(g: Grid, p: Params, I0, I1, v0=None, gn_maxit=5, pcg_maxit=10, pcg_
     gmax = None
     for n_it in range(gn_maxit):
         gl2, E, _, _, tr = gradient(g, p, v, I0, I1)
+        if exact_gradient:
+            gl2 = gradient_exact(g, p, v, I0, I1)[0]
         gsp = to_space(g, p, gl2)
         gmax = float(np.abs(gsp).max())
         if g0max is None:
@@ -549,7 +554,7 @@ def register(g: Grid, p: Params, I0, I1, v0=None, gn_maxit=5, pcg_maxit=10, pcg_
         v = v + eps * x
     Ef, _, _, trf = energy(g, p, v, I0, I1)
     energies.append(Ef)
-    gl2f = gradient(g, p, v, I0, I1)[0]
+    gl2f = gradient_exact(g, p, v, I0, I1)[0] if exact_gradient else gradient(g, p, v, I0, I1)[0]
     gnorm_rel = float(np.abs(to_space(g, p, gl2f)).max() / g0max) if g0max else 0.0
     mse = g.dot(trf.m1 - I1, trf.m1 - I1) / g.dot(I0 - I1, I0 - I1)
     J = jacobian_det(g, trf.u)

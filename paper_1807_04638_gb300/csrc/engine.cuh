@@ -29,6 +29,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "fft_fast.cuh"
 #include "fft_kernels.cuh"
@@ -36,6 +38,16 @@
 #include "pw_kernels.cuh"
 
 namespace lddmm {
+
+// NVTX range around a stage of the path (shoot, sweeps, gradient, Hv, GN and
+// PCG iterations), visible to a profiler attached to the process; without
+// one the push and pop cost a function-pointer test.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Kernel classes for the optional CUDA-event profiler.
 enum KClass { KC_AX0 = 0, KC_AX1, KC_AX2, KC_ADSTAR, KC_TANPW, KC_ADJPW, KC_SL, KC_WARP, KC_RED, KC_SPEC, KC_MISC, KC_COUNT };
@@ -1079,6 +1091,7 @@ class Engine : public EngineBase {
 
     // v0 real -> stores the stage fields, u1 in ubuf[nt%2], kinetic in dres[0..nt]
     void shoot_core(const T* v0, bool kinetic) {
+        NvtxRange nr_("lddmm shoot");
         const double dt_ = dt();
         const int nt = prm.nt;
         const GridI gi{d.n0, d.n1, d.n2};
@@ -1144,6 +1157,7 @@ class Engine : public EngineBase {
     // ------------------------------------------------------------ Jacobi sweeps
     // tangent: from tan_[0] = (eta0, xi0); result in tan_[nt % 2]
     void tangent_sweep() {
+        NvtxRange nr_("lddmm tangent sweep");
         const double dt_ = dt();
         T* E = rs;                  // 24 fields
         T* X = rs + 24 * d.N;       // 12 fields
@@ -1218,6 +1232,7 @@ class Engine : public EngineBase {
     // eta_src (nullable): real cotangents on eta_k, k = 0..nt (3 fields each),
     // added to ybar_eta after the transposed step k (exact discrete gradient)
     void adjoint_sweep(const T* eta_src = nullptr) {
+        NvtxRange nr_("lddmm adjoint sweep");
         const double dt_ = dt();
         T* Y = rs;              // 6 fields
         T* G = rs + 6 * d.N;    // 36 fields
@@ -1356,6 +1371,7 @@ class Engine : public EngineBase {
 
     // gradient internals: E into dres[nt+1..nt+3]; gradient real in metric `space`
     void gradient_core(const T* v0, const T* I0, const T* I1, T* grad, int space) {
+        NvtxRange nr_("lddmm gradient");
         shoot_core(v0, true);
         warp_and_grad(I0);
         {
@@ -1388,6 +1404,7 @@ class Engine : public EngineBase {
         lin_valid = true;
     }
     void hessvec_core(const T* dv0, T* out, int space) {
+        NvtxRange nr_("lddmm hessvec");
         fwd_vec(dv0, dhat);
         mask_copy(dhat, tan_[0]);
         cudaMemsetAsync(tan_[0] + 3 * d.NS, 0, 3 * d.NS * sizeof(C), st);

@@ -233,6 +233,25 @@ def test_gradient_discrete_matches_oracle(pkg, prec, kind, n):
     assert rel(got, want) < tol, rel(got, want)
 
 
+def test_register_with_discrete_gradient_replays_oracle(pkg):
+    """Gauss-Newton-Krylov with the exact discrete gradient: the FP64 GPU run
+    and the oracle make the same PCG and Armijo decisions and reach the same
+    v0."""
+    n = (16, 12, 10)
+    nt = 4
+    g, I0, I1, vtrue = problem(n, 12, nt)
+    p = O.Params(nt=nt)
+    prm = params(pkg, "f64", nt=nt, gn_maxit=3, pcg_maxit=6, gradient_mode=pkg.LDDMM_GRAD_DISCRETE)
+    with pkg.Handle(n, prm) as h:
+        v = torch.zeros((3,) + n, dtype=torch.float64, device="cuda")
+        rep = h.lddmm_register(dev(I0, torch.float64), dev(I1, torch.float64), v)
+    ref = O.register(g, p, I0, I1, gn_maxit=3, pcg_maxit=6, exact_gradient=True)
+    assert rep["pcg_iters"] == ref.pcg_iters and rep["step"] == ref.steps
+    assert rel(host(v), ref.v0) < 1e-9
+    assert np.allclose(rep["energy"], ref.energies, rtol=1e-9)
+    assert abs(rep["gnorm_rel"] - ref.gnorm_rel) < 1e-9 and abs(rep["mse_rel"] - ref.mse_rel) < 1e-9
+
+
 def test_gradient_discrete_finite_differences_on_gpu(pkg):
     """The FP64 GPU exact gradient against central differences of the GPU's own
     energy in rough random directions."""
