@@ -392,6 +392,12 @@ def run_native(args, rank, world):
         "kernel_shares": shares,
         "result_finite": finite,
     }
+    # the characterisations beside the headline (precision and solver forms,
+    # serving, CPU baseline) run at N = 1 only, so a multi-GPU run holds its
+    # GPUs for the timed work alone
+    if world > 1:
+        args.no_fp64, args.no_cpu = True, True
+        args.registrations, args.serve_requests = 0, 0
     return finish(args, out, h, v0t, d, I0, I1, stream, dev, rank, P, NG)
 
 
