@@ -1,0 +1,54 @@
+"""Writes the stored expected values under tests/golden/ by calling the FP64
+oracle only (no GPU code).  Run from the repository root:
+
+    python tests/golden/make_golden.py
+
+config1_register_32cubed.json: the plain-method registration of the 32^3
+blob-phantom workload (seed 0; target = the oracle's shoot of a random
+|k| <= 4 velocity with a 2-voxel peak displacement; nt = 10,
+K = (Id - 0.01 Lap)^-2, weight 1e-3, 5 Gauss-Newton iterations of at most
+10 PCG iterations, PCG relative tolerance 0.1, Catmull-Rom transport, V
+metric): the oracle's energy trace, PCG counts, Armijo steps and final
+metrics, plus the energy and gradient norm at v0 = 0.
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from oracle import lddmm_oracle as O  # noqa: E402
+from paper_1807_04638_gb300 import synth  # noqa: E402
+
+
+def config1_inputs():
+    n, nt = (32, 32, 32), 10
+    g = O.Grid(n, alpha=0.01)
+    I0, vtrue = synth.blob_pair_inputs(n, 0, kmax=4, max_disp_vox=2.0)
+    I1 = O.shoot(g, vtrue, nt, I0).m1
+    return g, O.Params(alpha=0.01, nt=nt, weight=1e-3), I0, I1
+
+
+def main():
+    g, p, I0, I1 = config1_inputs()
+    zero = np.zeros((3,) + g.n)
+    g0, E0 = O.gradient(g, p, zero, I0, I1)[:2]
+    rep = O.register(g, p, I0, I1, gn_maxit=5, pcg_maxit=10, pcg_rtol=0.1)
+    out = {
+        "what": "config-1 plain-method registration, 32^3, FP64 oracle",
+        "E_at_zero": E0, "grad_L2_norm_at_zero": float(np.sqrt(g.dot(g0, g0))),
+        "energies": rep.energies, "pcg_iters": rep.pcg_iters, "steps": rep.steps,
+        "gnorm_rel": rep.gnorm_rel, "mse_rel": rep.mse_rel, "jac_min": rep.jac_min, "jac_max": rep.jac_max,
+        "v0_l2_norm": float(np.sqrt(g.dot(rep.v0, rep.v0))),
+    }
+    with open(os.path.join(HERE, "config1_register_32cubed.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
