@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--nt", type=int, default=NT, help="time steps (profiling runs; the metric uses 10)")
     ap.add_argument("--serve-requests", type=int, default=8,
                     help="requests of the serving trace (0: skip); the full serving workload is 256")
+    ap.add_argument("--plain-registration", action="store_true",
+                    help="also run the registration of the workload with the plain FP64 method")
     ap.add_argument("--serve-fp64", type=int, default=0,
                     help="also run the first M serving requests serially with the plain FP64 method")
     return ap.parse_args()
@@ -621,6 +623,24 @@ def finish(args, out, h, v0t, d, I0, I1, stream, dev, rank, P, NG):
                                           "pcg_iters_total": rl["pcg_iters_total"], "mse_rel": rl["mse_rel"],
                                           "gnorm_rel": rl["gnorm_rel"], "jac_min": rl["jac_min"],
                                           "jac_max": rl["jac_max"], "status": rl["status"]}
+
+    # ---- the same registration with the plain FP64 method (opt-in: about
+    # ten times the FP32 form's time)
+    if args.plain_registration and rank == 0:
+        prm64 = pkg.default_params(**{f: getattr(prm, f) for f, _ in prm._fields_})
+        prm64.compute_dtype, prm64.state_dtype = pkg.LDDMM_F64, pkg.LDDMM_F64
+        h64 = pkg.Handle(NG, prm64, stream=stream, device=dev.index)
+        v = torch.zeros((3,) + NG, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r64 = h64.lddmm_register(I0.double(), I1.double(), v)
+        torch.cuda.synchronize(dev)
+        t64 = time.perf_counter() - t0
+        h64.close()
+        out["registration_plain_fp64"] = {"seconds": t64, "gn_iters": r64["gn_iters"],
+                                          "pcg_iters_total": r64["pcg_iters_total"], "mse_rel": r64["mse_rel"],
+                                          "gnorm_rel": r64["gnorm_rel"], "jac_min": r64["jac_min"],
+                                          "jac_max": r64["jac_max"], "status": r64["status"]}
 
     # ---- serving trace (continuous batching, mixed grid sizes)
     if args.serve_requests > 0 and rank == 0:
