@@ -56,6 +56,21 @@ def test_host_side_checks_without_gpu(libpath):
     assert lib.lddmm_create(None, ctypes.byref(g), ctypes.byref(p), None) == 1  # ARG
     assert lib.lddmm_shoot(None, None, None, None, None, None) == 1
     assert lib.lddmm_status_string(5).decode().startswith("no linearisation")
+    # parameter combinations the library refuses before any device work
+    ok = pkg.default_params(compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32)
+    assert pkg.workspace_bytes((32, 32, 32), ok) > 0
+    for kw in (dict(optimizer=2), dict(gradient_mode=2), dict(dealias=2), dict(checkpoint_every=0),
+               dict(state_dtype=pkg.LDDMM_BF16, gradient_mode=pkg.LDDMM_GRAD_DISCRETE),
+               dict(checkpoint_every=2, gradient_mode=pkg.LDDMM_GRAD_DISCRETE)):
+        bad = pkg.default_params(compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32)
+        for k, v in kw.items():
+            setattr(bad, k, v)
+        assert pkg.workspace_bytes((32, 32, 32), bad) == 0, kw
+    # the exact discrete gradient keeps every map and every dE/dv_k
+    ex = pkg.default_params(compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32,
+                            gradient_mode=pkg.LDDMM_GRAD_DISCRETE)
+    extra = pkg.workspace_bytes((32, 32, 32), ex) - pkg.workspace_bytes((32, 32, 32), ok)
+    assert extra == (6 * (ok.nt + 1) + 6) * 32 ** 3 * 4
     # the FP64 rate probe checks its arguments before launching
     assert lib.lddmm_probe_fp64_fma(None, 1, 1, None) == 1
     thr = lib.lddmm_probe_fp64_fma_threads()
