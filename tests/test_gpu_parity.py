@@ -277,6 +277,44 @@ def test_gradient_discrete_finite_differences_on_gpu(pkg):
             assert abs(g.dot(gnp, d) - fd) < 1e-7 * abs(fd)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n", [(12, 10, 15), (32, 32, 32)])
+def test_degenerate_cases(pkg, prec, n):
+    """The method's degenerate cases on the GPU: v0 = 0 is the identity map
+    (u1 = 0 and m1 = I0 bit for bit, zero kinetic energy); a constant
+    velocity of whole voxels per unit time is a rigid roll of the image; at
+    v0 = 0 the tangent sweep gives eta1 = xi1 = P delta (eta constant,
+    xi' = eta over unit time)."""
+    dtype, _ = DT[prec]
+    g = O.Grid(n, alpha=0.01)
+    I0 = synth.spectral_gaussian_smooth(synth.blob_phantom(n, synth.rng_for(90)), 1.0)
+    I0d = dev(I0, dtype)
+    tol = 1e-12 if prec == "f64" else 1e-5
+    with pkg.Handle(n, params(pkg, prec, nt=4)) as h:
+        m1, u1 = h.new_img(), h.new_vec()
+        kin = h.lddmm_shoot(dev(np.zeros((3,) + n), dtype), I0d, m1, u1, kinetic=True)
+        h.lddmm_synchronize()
+        assert torch.equal(u1, torch.zeros_like(u1))
+        assert torch.equal(m1, I0d)
+        assert all(k == 0.0 for k in kin)
+        # whole-voxel constant velocity: (2, -1, 3) voxels over unit time
+        shift = (2, -1, 3)
+        vc = np.stack([np.full(n, s * g.h[a]) for a, s in enumerate(shift)])
+        h.lddmm_shoot(dev(vc, dtype), I0d, m1, u1)
+        h.lddmm_synchronize()
+        want = np.roll(I0, shift, axis=(0, 1, 2))
+        assert rel(host(m1), want) < tol
+        assert rel(host(u1), -vc) < tol
+        # sweeps at v0 = 0
+        d = synth.band_limited_field(n, synth.rng_for(91), 6.0, 3) + 0.1 * synth.rng_for(92).standard_normal((3,) + n)
+        z = dev(np.zeros((3,) + n), dtype)
+        h.lddmm_shoot(z, I0d, m1)
+        e1, x1 = h.new_vec(), h.new_vec()
+        h.lddmm_jacobi_forward(dev(d, dtype), e1, x1)
+        h.lddmm_synchronize()
+        assert rel(host(e1), g.P(d)) < tol and rel(host(x1), g.P(d)) < tol
+
+
 def test_errors_are_reported(pkg):
     n = (8, 8, 8)
     with pytest.raises(pkg.LddmmError):
