@@ -233,6 +233,29 @@ def test_gradient_discrete_matches_oracle(pkg, prec, kind, n):
     assert rel(got, want) < tol, rel(got, want)
 
 
+@pytest.mark.parametrize("n", [(16, 12, 10), (32, 32, 32)])
+def test_register_fp32_form_replayed_in_oracle(pkg, n):
+    """Whole registration in the FP32 form: the oracle replays the GPU's
+    decisions (PCG iterations and Armijo steps per Gauss-Newton iteration)
+    in FP64, and the outcomes agree within the FP32 form's tolerances
+    (final residual and Jacobian extrema 1e-4, energies 1e-5)."""
+    nt = 4
+    g, I0, I1, vtrue = problem(n, 14, nt)
+    p = O.Params(nt=nt)
+    f32 = torch.float32
+    prm = params(pkg, "f32", nt=nt, gn_maxit=3, pcg_maxit=6)
+    with pkg.Handle(n, prm) as h:
+        v = torch.zeros((3,) + n, dtype=f32, device="cuda")
+        rep = h.lddmm_register(dev(I0, f32), dev(I1, f32), v)
+        v32 = host(v)
+    trace = list(zip(rep["pcg_iters"], rep["step"]))
+    ref = O.register(g, p, I0, I1, gn_maxit=3, pcg_maxit=6, replay=trace)
+    assert rel(v32, ref.v0) < 1e-4
+    assert np.allclose(rep["energy"], ref.energies, rtol=1e-5, atol=0)
+    assert abs(rep["mse_rel"] - ref.mse_rel) < 1e-4 * ref.mse_rel
+    assert abs(rep["jac_min"] - ref.jac_min) < 1e-4 and abs(rep["jac_max"] - ref.jac_max) < 1e-4
+
+
 def test_register_with_discrete_gradient_replays_oracle(pkg):
     """Gauss-Newton-Krylov with the exact discrete gradient: the FP64 GPU run
     and the oracle make the same PCG and Armijo decisions and reach the same
