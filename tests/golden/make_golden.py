@@ -1,7 +1,14 @@
 """Writes the stored expected values under tests/golden/ by calling the FP64
 oracle only (no GPU code).  Run from the repository root:
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [config1] [bench128]
+
+bench128_samples.json: the 128^3 benchmark workload (nested ellipsoids,
+seed 1; target = the oracle's shoot of the true velocity plus noise; nt = 10,
+K = (Id - 0.005 Lap)^-2, weight 1e-3, V metric): the energy, the L2 norms of
+the V gradient and of the V Hessian-vector product at v0 = v0_true / 2 in
+the direction of the workload, and their values at 2048 seeded sample
+points (about 12 minutes of CPU).
 
 config1_register_32cubed.json: the plain-method registration of the 32^3
 blob-phantom workload (seed 0; target = the oracle's shoot of a random
@@ -33,7 +40,38 @@ def config1_inputs():
     return g, O.Params(alpha=0.01, nt=nt, weight=1e-3), I0, I1
 
 
-def main():
+def bench128_inputs():
+    """The 128^3 workload's arrays (the same recipe and seeds as the
+    benchmark) and the sample points."""
+    from paper_1807_04638_gb300 import synth as S
+    n = (128, 128, 128)
+    P, v0t, e0, e1 = S.ellipsoid_pair_inputs(n, 1, kmax=6, max_disp_vox=6.0, noise_sigma=0.02)
+    d = S.band_limited_field(n, S.rng_for(1 + 1000), 6.0, 3) * (2 * np.pi / n[0])
+    idx = S.rng_for(4242).integers(0, 3 * int(np.prod(n)), 2048)
+    return n, P, v0t, e0, e1, d, idx
+
+
+def bench128():
+    n, P, v0t, e0, e1, d, idx = bench128_inputs()
+    g = O.Grid(n, alpha=0.005)
+    p = O.Params(alpha=0.005, nt=10, weight=1e-3)
+    I0 = P + e0
+    I1 = O.shoot(g, v0t, p.nt, P).m1 + e1
+    gl2, E, _, _, tr = O.gradient(g, p, 0.5 * v0t, I0, I1)
+    gV = O.to_space(g, p, gl2)
+    hV = O.to_space(g, p, O.hessvec(g, p, tr, d))
+    out = {
+        "what": "128^3 benchmark workload, FP64 oracle, v0 = v0_true / 2, V metric",
+        "E": E, "grad_V_l2": float(np.linalg.norm(gV)), "hv_V_l2": float(np.linalg.norm(hV)),
+        "idx": [int(i) for i in idx], "grad_V": [float(x) for x in gV.ravel()[idx]],
+        "hv_V": [float(x) for x in hV.ravel()[idx]],
+    }
+    with open(os.path.join(HERE, "bench128_samples.json"), "w") as f:
+        json.dump(out, f)
+    print("bench128: E", E)
+
+
+def config1():
     g, p, I0, I1 = config1_inputs()
     zero = np.zeros((3,) + g.n)
     g0, E0 = O.gradient(g, p, zero, I0, I1)[:2]
@@ -51,4 +89,8 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    which = sys.argv[1:] or ["config1", "bench128"]
+    if "config1" in which:
+        config1()
+    if "bench128" in which:
+        bench128()

@@ -5,7 +5,10 @@ from the FP64 oracle alone).
   the 32^3 plain-method workload at v0 = 0 (regression of the oracle);
 * GPU: the FP64 library runs the whole plain-method registration of that
   workload (nt = 10, 5 Gauss-Newton x <= 10 PCG) with the oracle's
-  decisions, energies and final metrics.
+  decisions, energies and final metrics;
+* GPU: on the 128^3 benchmark workload, in the configuration the benchmark
+  times (FP32 form, nt = 10), the V gradient and the V Hessian-vector
+  product match the oracle at 2048 stored sample points.
 """
 import json
 import os
@@ -24,12 +27,16 @@ def _load():
         return json.load(f)
 
 
-def _inputs():
+def _mg():
     import importlib.util
     spec = importlib.util.spec_from_file_location("make_golden", os.path.join(HERE, "golden", "make_golden.py"))
     mg = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mg)
-    return mg.config1_inputs()
+    return mg
+
+
+def _inputs():
+    return _mg().config1_inputs()
 
 
 def test_oracle_reproduces_stored_config1_start():
@@ -61,3 +68,40 @@ def test_gpu_config1_registration_matches_stored_trace():
     for k in ("mse_rel", "gnorm_rel", "jac_min", "jac_max"):
         assert abs(rep[k] - ref[k]) < 1e-9 * max(1.0, abs(ref[k])), k
     assert abs(np.sqrt(g.dot(vn, vn)) - ref["v0_l2_norm"]) < 1e-9 * ref["v0_l2_norm"]
+
+
+@pytest.mark.gpu
+def test_gpu_bench128_gradient_and_hv_at_sampled_points():
+    """Full size, benchmark configuration: the FP32 V gradient and V Hv at
+    v0 = v0_true / 2 against the oracle at the stored sample points (relative
+    L2 over the samples 1e-5), and the energy and full-array norms to 1e-5."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1807_04638_gb300 as pkg
+    with open(os.path.join(HERE, "golden", "bench128_samples.json")) as f:
+        ref = json.load(f)
+    n, P, v0t, e0, e1, d, idx = _mg().bench128_inputs()
+    assert [int(i) for i in idx] == ref["idx"]
+    f64, f32 = torch.float64, torch.float32
+    # target: the FP64 library shoot of the true velocity (the oracle's to
+    # about 1e-10) plus the stored-recipe noise
+    with pkg.Handle(n, pkg.default_params(alpha=0.005, nt=10)) as h64:
+        m1 = h64.new_img()
+        h64.lddmm_shoot(torch.tensor(v0t, dtype=f64, device="cuda"), torch.tensor(P, dtype=f64, device="cuda"), m1)
+        h64.lddmm_synchronize()
+        I1 = m1.cpu().numpy() + e1
+    prm = pkg.default_params(alpha=0.005, nt=10, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=f32, device="cuda")
+    with pkg.Handle(n, prm) as h:
+        grad, hv = h.new_vec(), h.new_vec()
+        e = h.lddmm_gradient(T(0.5 * v0t), T(P + e0), T(I1), grad)
+        h.lddmm_hessvec(T(d), hv)
+        h.lddmm_synchronize()
+        gn, hn = grad.double().cpu().numpy(), hv.double().cpu().numpy()
+    rel = lambda a, b: float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+    assert abs(e[0] - ref["E"]) < 1e-5 * ref["E"]
+    assert rel(gn.ravel()[idx], ref["grad_V"]) < 1e-5
+    assert rel(hn.ravel()[idx], ref["hv_V"]) < 1e-5
+    assert abs(np.linalg.norm(gn) - ref["grad_V_l2"]) < 1e-5 * ref["grad_V_l2"]
+    assert abs(np.linalg.norm(hn) - ref["hv_V_l2"]) < 1e-5 * ref["hv_V_l2"]
