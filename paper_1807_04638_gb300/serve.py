@@ -57,39 +57,31 @@ def _key(n, p: N.lddmm_params, lengths):
     return (tuple(n), tuple(lengths) if lengths else None) + tuple(getattr(p, f) for f, _ in p._fields_)
 
 
-class Server:
-    """Admission by HBM budget, one stream per in-flight registration."""
+class HandlePool:
+    """HBM-budget accounting of the live handles of a server: the ones in
+    use and the ones parked for reuse by a later request with the same key
+    (grid and parameters).  A handle is a pair (object with close(), bytes).
+    The pool itself takes no lock; the server calls it under its own."""
 
-    def __init__(self, budget_bytes: float = 80e9, max_inflight: int = 8, device: int = 0):
-        import torch
-        self.torch = torch
+    def __init__(self, budget_bytes: float):
         self.budget = float(budget_bytes)
-        self.max_inflight = int(max_inflight)
-        self.device = torch.device("cuda", device)
-        self.lock = threading.Condition()
-        self.used = 0.0                       # bytes of live handles (busy + parked)
-        self.inflight = 0
-        self.parked: Dict[tuple, List[Tuple[N.Handle, int]]] = {}
-        self.results: Dict[int, Result] = {}
-        self.t0 = None
-        self.threads: List[threading.Thread] = []
+        self.used = 0.0                        # bytes of live handles (busy + parked)
         self.peak_used = 0.0
-        self.peak_inflight = 0
+        self.parked: Dict[tuple, List[Tuple[object, int]]] = {}
 
-    # -- memory accounting ------------------------------------------------------
-    def _acquire_handle(self, req: Request) -> Optional[Tuple[N.Handle, int]]:
-        """Called with the lock held; returns a handle or None if it must wait."""
-        n = req.I0.shape
-        k = _key(n, req.params, req.lengths)
-        pool = self.parked.get(k)
+    def acquire(self, key, need: int, make):
+        """A parked handle of `key`, else a new one from make() once `need`
+        bytes fit the budget, closing parked handles of other keys to make
+        room.  Returns (handle, bytes); None when the request must wait for
+        handles in use to be released; raises ValueError when it can never
+        fit."""
+        pool = self.parked.get(key)
         if pool:
             return pool.pop()
-        need = N.workspace_bytes(n, req.params, req.lengths)
         if need <= 0:
             raise ValueError("invalid request shape or parameters")
         if need > self.budget:
             raise ValueError(f"exceeds the HBM budget ({need / 1e9:.1f} GB > {self.budget / 1e9:.1f} GB)")
-        # evict parked handles of other shapes until the new one fits
         while self.used + need > self.budget:
             victim = next((kk for kk, v in self.parked.items() if v), None)
             if victim is None:
@@ -97,16 +89,62 @@ class Server:
             h, b = self.parked[victim].pop()
             h.close()
             self.used -= b
-        with self.torch.cuda.device(self.device):
-            stream = self.torch.cuda.Stream(device=self.device)
-            h = N.Handle(n, req.params, lengths=req.lengths, stream=stream, device=self.device.index)
+        h = make()
         self.used += need
         self.peak_used = max(self.peak_used, self.used)
         return h, need
 
+    def park(self, key, hb):
+        self.parked.setdefault(key, []).append(hb)
+
+    def drop(self, hb):
+        """Close a handle that is not to be reused (its request failed)."""
+        hb[0].close()
+        self.used -= hb[1]
+
+    def close_parked(self):
+        for pool in self.parked.values():
+            for h, b in pool:
+                h.close()
+                self.used -= b
+        self.parked.clear()
+
+
+class Server:
+    """Admission by HBM budget, one stream per in-flight registration."""
+
+    def __init__(self, budget_bytes: float = 80e9, max_inflight: int = 8, device: int = 0):
+        import torch
+        self.torch = torch
+        self.pool = HandlePool(budget_bytes)
+        self.max_inflight = int(max_inflight)
+        self.device = torch.device("cuda", device)
+        self.lock = threading.Condition()
+        self.inflight = 0
+        self.results: Dict[int, Result] = {}
+        self.t0 = None
+        self.threads: List[threading.Thread] = []
+        self.peak_inflight = 0
+
+    @property
+    def peak_used(self) -> float:
+        return self.pool.peak_used
+
+    # -- memory accounting ------------------------------------------------------
+    def _acquire_handle(self, req: Request) -> Optional[Tuple[N.Handle, int]]:
+        """Called with the lock held; returns a handle or None if it must wait."""
+        n = req.I0.shape
+        k = _key(n, req.params, req.lengths)
+
+        def make():
+            with self.torch.cuda.device(self.device):
+                stream = self.torch.cuda.Stream(device=self.device)
+                return N.Handle(n, req.params, lengths=req.lengths, stream=stream, device=self.device.index)
+
+        return self.pool.acquire(k, N.workspace_bytes(n, req.params, req.lengths), make)
+
     def _release_handle(self, req: Request, hb):
-        k = _key(req.I0.shape, req.params, req.lengths)
-        self.parked.setdefault(k, []).append(hb)
+        self.pool.park(_key(req.I0.shape, req.params, req.lengths), hb)
 
     # -- request execution ------------------------------------------------------
     def _run(self, req: Request, hb):
@@ -132,8 +170,7 @@ class Server:
             sticky = N.lib().lddmm_last_status(h._h) if h._h else 0
             with self.lock:
                 if sticky != 0:  # a failed handle is not reused
-                    h.close()
-                    self.used -= hb[1]
+                    self.pool.drop(hb)
                 else:
                     self._release_handle(req, hb)
                 self.inflight -= 1
@@ -196,11 +233,7 @@ class Server:
 
     def close(self):
         with self.lock:
-            for pool in self.parked.values():
-                for h, b in pool:
-                    h.close()
-                    self.used -= b
-            self.parked.clear()
+            self.pool.close_parked()
 
 
 def serial(requests: List[Request], device: int = 0) -> List[Result]:
