@@ -12,6 +12,12 @@ Every batch member owns a handle (its stored time states are the backward's
 linearisation point), created on its own CUDA stream so that the members'
 sweeps overlap on the device; the Function orders those streams after the
 caller's stream on entry and before it on exit.
+
+Memory: with ``max_bytes`` the Shooter keeps every forward state while the
+batch's workspaces fit, and otherwise stores the spectral velocity every 2
+steps and recomputes the states segment by segment inside the backward
+(checkpoint_every = 2: the smallest footprint, at one extra shoot per
+backward whatever the segment length); the gradient is unchanged.
 """
 from __future__ import annotations
 
@@ -26,17 +32,34 @@ class Shooter:
     """Handles for a batch of ``batch`` registrations on one grid."""
 
     def __init__(self, n: Sequence[int], batch: int, params: Optional[N.lddmm_params] = None,
-                 lengths=None, device=None):
+                 lengths=None, device=None, max_bytes: Optional[float] = None):
         self.n = tuple(int(x) for x in n)
         self.batch = int(batch)
         self.params = params if params is not None else N.default_params(
             compute_dtype=N.LDDMM_F32, state_dtype=N.LDDMM_F32)
+        if max_bytes is not None:
+            self.params = self.plan_memory(self.n, self.batch, self.params, max_bytes, lengths)
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.device = dev
         self.streams = [torch.cuda.Stream(device=dev) for _ in range(self.batch)]
         self.handles = [N.Handle(self.n, self.params, lengths=lengths, stream=s, device=dev.index)
                         for s in self.streams]
         self.dtype = self.handles[0].dtype
+
+    @staticmethod
+    def plan_memory(n, batch, params, max_bytes, lengths=None):
+        """A copy of params that keeps every forward state if batch
+        workspaces fit max_bytes, else checkpoints every 2 steps; raises
+        MemoryError when even that does not fit."""
+        p = N.default_params(**{f: getattr(params, f) for f, _ in params._fields_})
+        if batch * N.workspace_bytes(n, p, lengths) <= max_bytes:
+            return p
+        if p.nt > 2:
+            p.checkpoint_every = 2
+            if batch * N.workspace_bytes(n, p, lengths) <= max_bytes:
+                return p
+        raise MemoryError(f"{batch} x {N.workspace_bytes(n, p, lengths) / 1e9:.2f} GB exceeds "
+                          f"{max_bytes / 1e9:.2f} GB even with checkpointed states")
 
     def close(self):
         for h in self.handles:

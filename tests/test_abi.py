@@ -75,3 +75,20 @@ def test_host_side_checks_without_gpu(libpath):
     assert lib.lddmm_probe_fp64_fma(None, 1, 1, None) == 1
     thr = lib.lddmm_probe_fp64_fma_threads()
     assert lib.lddmm_probe_fp64_fma_flops(3, 5) == 2 * 8 * 5 * thr * 3
+
+
+def test_autograd_memory_plan_without_gpu(libpath):
+    """The differentiation form keeps every forward state while the batch's
+    workspaces fit, else checkpoints every 2 steps (less than half the
+    memory at nt = 10), else refuses."""
+    import paper_1807_04638_gb300 as pkg
+    from paper_1807_04638_gb300.autograd import Shooter
+    p = pkg.default_params(compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32, nt=10)
+    n = (96, 96, 96)
+    full = pkg.workspace_bytes(n, p)
+    assert Shooter.plan_memory(n, 8, p, 8 * full).checkpoint_every == 1
+    q = Shooter.plan_memory(n, 8, p, 8 * full - 1)
+    assert q.checkpoint_every == 2 and pkg.workspace_bytes(n, q) < 0.5 * full
+    assert p.checkpoint_every == 1  # the caller's parameters are not changed
+    with pytest.raises(MemoryError):
+        Shooter.plan_memory(n, 8, p, 8 * pkg.workspace_bytes(n, q) - 1)

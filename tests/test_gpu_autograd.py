@@ -77,6 +77,35 @@ def test_backward_matches_oracle(pkg, prec):
         assert rel(got[b], want) < tol, (b, rel(got[b], want))
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_checkpointed_backward_equals_stored_states(pkg, prec):
+    """When the memory budget asks for it the Shooter checkpoints the forward
+    states (every 2 steps) and recomputes them in the backward: the loss
+    and the gradient are the same as with every state stored."""
+    from paper_1807_04638_gb300.autograd import Shooter, shoot
+    n, nt, alpha = (32, 32, 32), 6, 0.01
+    g, I0, I1, v0 = batch_inputs(n, [21, 22], 2, 1.5, nt, alpha)
+    cd = pkg.LDDMM_F32 if prec == "f32" else pkg.LDDMM_F64
+    dt = torch.float32 if prec == "f32" else torch.float64
+    prm = pkg.default_params(alpha=alpha, nt=nt, compute_dtype=cd, state_dtype=cd)
+    full = pkg.workspace_bytes(n, prm)
+    out = []
+    for budget in (None, 2 * full - 1):
+        sh = Shooter(n, 2, prm, max_bytes=budget)
+        try:
+            assert sh.params.checkpoint_every == (1 if budget is None else 2)
+            v = torch.tensor(v0, dtype=dt, device="cuda", requires_grad=True)
+            loss = ((shoot(v, torch.tensor(I0, dtype=dt, device="cuda"), sh)
+                     - torch.tensor(I1, dtype=dt, device="cuda")) ** 2).sum()
+            loss.backward()
+            torch.cuda.synchronize()
+            out.append((float(loss.detach()), v.grad.double().cpu().numpy()))
+        finally:
+            sh.close()
+    assert out[0][0] == out[1][0]
+    assert rel(out[1][1], out[0][1]) < 1e-12
+
+
 def test_backward_vs_finite_differences(pkg):
     from paper_1807_04638_gb300.autograd import Shooter, shoot
     n, nt, alpha = (24, 24, 24), 8, 0.01
