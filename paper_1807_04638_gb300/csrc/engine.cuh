@@ -341,6 +341,7 @@ class Engine : public EngineBase {
     bool fast[3] = {false, false, false};
     // band-limited transforms (all three passes register-blocked, dealiasing on)
     bool band_ok = false;
+    bool sl_staged = false;  // FP32 map steps use k_sl_step_staged
     int bnb2 = 0, bc1 = 0, bs1 = 0;
     size_t smem_c[2], smem2;
     int pool_top = 0;
@@ -580,6 +581,9 @@ class Engine : public EngineBase {
         bc1 = (tabs.kcut[1] + 2) & ~1;
         bs1 = (d.n1 - tabs.kcut[1]) & ~1;
         if (bc1 >= bs1) bc1 = bs1 = d.n1;
+        if constexpr (sizeof(T) == 4)
+            sl_staged = raise_smem_limit(k_sl_step_staged<true>, SLBox<true>::SMEM) &&
+                        raise_smem_limit(k_sl_step_staged<false>, SLBox<false>::SMEM);
         band_ok = prm.dealias && fast[0] && fast[1] && fast[2] && !force_full_band() &&
                   (bnb2 < d.n2h || bc1 < bs1);
         LD_CK(cudaDeviceSynchronize());
@@ -1020,6 +1024,26 @@ class Engine : public EngineBase {
         return status;
     }
 
+    // One semi-Lagrangian map step u0 -> u1 (velocities v0 at t_k, v1 at
+    // t_{k+1}): the shared-memory staged kernel in FP32, the plain gather
+    // kernel in FP64 (or if the staged kernel's shared memory was refused).
+    void sl_step(const GridI& gi, const T* v0, const T* v1, const T* u0, T* u1, T dt_, T ih0, T ih1, T ih2,
+                 int cubic) {
+        if constexpr (sizeof(T) == 4) {
+            if (sl_staged) {
+                const dim3 grid((d.n2 + SLT2 - 1) / SLT2, (d.n1 + SLT1 - 1) / SLT1, (d.n0 + SLT0 - 1) / SLT0);
+                if (cubic)
+                    k_sl_step_staged<true><<<grid, SLT1 * SLT2, SLBox<true>::SMEM, st>>>(gi, v0, v1, u0, u1, dt_, ih0,
+                                                                                          ih1, ih2, d.N);
+                else
+                    k_sl_step_staged<false><<<grid, SLT1 * SLT2, SLBox<false>::SMEM, st>>>(gi, v0, v1, u0, u1, dt_,
+                                                                                            ih0, ih1, ih2, d.N);
+                return;
+            }
+        }
+        k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, v0, v1, u0, u1, dt_, ih0, ih1, ih2, cubic, d.N);
+    }
+
     // ------------------------------------------------------------ shooting
     // One Heun step of the EPDiff shooting from `cur` into `nxt`, storing the
     // fields of both stages.  With `transport` the semi-Lagrangian map step
@@ -1040,8 +1064,7 @@ class Engine : public EngineBase {
         if (kinetic) dot_async(S1 + 12 * d.N, S1, 3 * d.N, k, d.cell);
         if (transport && k >= 1) {
             PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
-            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vss[(k - 1) % 2], S1, ubuf_at(k - 1), ubuf_at(k),
-                                                             (T)dt_, ih0, ih1, ih2, cubic, d.N);
+            sl_step(gi, vss[(k - 1) % 2], S1, ubuf_at(k - 1), ubuf_at(k), (T)dt_, ih0, ih1, ih2, cubic);
         }
         {
             PScope ps_(this, KC_ADSTAR, adb);
@@ -1128,8 +1151,7 @@ class Engine : public EngineBase {
         if (kinetic) dot_async(vfin + 3 * d.N, vfin, 3 * d.N, nt, d.cell);
         {
             PScope ps_(this, KC_SL, 12.0 * d.N * sizeof(T));
-            k_sl_step<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(gi, vss[(nt - 1) % 2], vfin, ubuf_at(nt - 1),
-                                                             ubuf_at(nt), (T)dt_, ih0, ih1, ih2, cubic, d.N);
+            sl_step(gi, vss[(nt - 1) % 2], vfin, ubuf_at(nt - 1), ubuf_at(nt), (T)dt_, ih0, ih1, ih2, cubic);
         }
     }
     T* u1() const { return ubuf_at(prm.nt); }

@@ -230,6 +230,140 @@ __global__ void k_sl_step(GridI g, const T* __restrict__ v0, const T* __restrict
     }
 }
 
+// ---------------------------------------------------------------- staged map step (FP32)
+// The map step of k_sl_step with its two gathers served from shared memory.
+// A block owns an SLT0 x SLT1 x SLT2 tile of output points.  It stages the
+// sampled field (first v0, then u0) over the tile plus a halo of LO / HI
+// voxels as one float4 (x, y, z, 0) per grid point, so that a tap is one
+// 16-byte shared load instead of three scalar global loads.  A point whose
+// stencil leaves the staged box (more than SL_DMAX voxels of displacement in
+// the step) takes the global gather of interp_at instead, so any velocity is
+// handled; the taps and their summation order are those of interp_at.
+constexpr int SLT0 = 4, SLT1 = 8, SLT2 = 32;  // threads: SLT1 * SLT2 = 256, SLT0 points each
+constexpr int SL_DMAX = 1;                    // staged displacement per step, voxels
+template <bool CUBIC> struct SLBox {
+    static constexpr int TLO = CUBIC ? -1 : 0, CNT = CUBIC ? 4 : 2;  // tap offsets TLO .. TLO + CNT - 1
+    static constexpr int LO = SL_DMAX - TLO;                         // halo below the tile
+    static constexpr int HI = SL_DMAX + TLO + CNT - 1;               // halo above the tile
+    static constexpr int B0 = SLT0 + LO + HI, B1 = SLT1 + LO + HI, B2 = SLT2 + LO + HI;
+    static constexpr int SIZE = B0 * B1 * B2;
+    static constexpr size_t SMEM = (size_t)SIZE * sizeof(float4);
+};
+
+// stage the 3 planes of f over the box whose corner is (c0, c1, c2), periodic
+template <bool CUBIC>
+__device__ __forceinline__ void sl_stage(float4* S, const float* __restrict__ f, size_t N, GridI g, int c0, int c1,
+                                         int c2) {
+    using B = SLBox<CUBIC>;
+    // box coordinates lie in [-LO, n + B - LO): within one period of the grid
+    // when n >= B, so one compare and add wraps them; smaller grids take the
+    // general modulo
+    const bool near = g.n0 >= B::B0 && g.n1 >= B::B1 && g.n2 >= B::B2;
+    auto wrap = [near](int x, int n) { return near ? (x < 0 ? x + n : (x >= n ? x - n : x)) : wrapi(x, n); };
+    for (int e = threadIdx.x; e < B::SIZE; e += SLT1 * SLT2) {
+        const int b2 = e % B::B2, b1 = (e / B::B2) % B::B1, b0 = e / (B::B2 * B::B1);
+        const size_t o = ((size_t)wrap(c0 + b0, g.n0) * g.n1 + wrap(c1 + b1, g.n1)) * g.n2 + wrap(c2 + b2, g.n2);
+        S[e] = make_float4(__ldg(&f[o]), __ldg(&f[N + o]), __ldg(&f[2 * N + o]), 0.f);
+    }
+}
+
+// the 3 components of the interpolant at (i0,i1,i2) + d: from the staged box
+// when the whole stencil lies in it, else from global memory
+template <bool CUBIC>
+__device__ __forceinline__ void sl_interp(const float4* S, const float* __restrict__ f, size_t N, GridI g, int i0,
+                                          int i1, int i2, int c0, int c1, int c2, const float d[3], float* res) {
+    using B = SLBox<CUBIC>;
+    int base[3];
+    float w[3][4];
+    const int ii[3] = {i0, i1, i2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float fl = floorf(d[a]);
+        const float t = d[a] - fl;
+        base[a] = ii[a] + (int)fl;
+        if constexpr (CUBIC) {
+            cr_weights(t, w[a]);
+        } else {
+            w[a][0] = 1.f - t;
+            w[a][1] = t;
+        }
+    }
+    const int l0 = base[0] + B::TLO - c0, l1 = base[1] + B::TLO - c1, l2 = base[2] + B::TLO - c2;
+    const bool inside = l0 >= 0 && l1 >= 0 && l2 >= 0 && l0 + B::CNT <= B::B0 && l1 + B::CNT <= B::B1 &&
+                        l2 + B::CNT <= B::B2;
+    if (!inside) {
+        interp_at<float, 3>(f, N, g, i0, i1, i2, d, CUBIC ? 1 : 0, res);
+        return;
+    }
+    res[0] = res[1] = res[2] = 0.f;
+#pragma unroll
+    for (int a0 = 0; a0 < B::CNT; ++a0) {
+#pragma unroll
+        for (int a1 = 0; a1 < B::CNT; ++a1) {
+            const float w01 = w[0][a0] * w[1][a1];
+            const float4* row = S + ((l0 + a0) * B::B1 + (l1 + a1)) * B::B2 + l2;
+#pragma unroll
+            for (int a2 = 0; a2 < B::CNT; ++a2) {
+                const float ww = w01 * w[2][a2];
+                const float4 v = row[a2];
+                res[0] += ww * v.x;
+                res[1] += ww * v.y;
+                res[2] += ww * v.z;
+            }
+        }
+    }
+}
+
+// k_sl_step for FP32 with staged gathers: grid (ceil(n2/SLT2), ceil(n1/SLT1),
+// ceil(n0/SLT0)), SLT1 * SLT2 threads, SLBox<CUBIC>::SMEM dynamic shared bytes
+template <bool CUBIC>
+__global__ void __launch_bounds__(SLT1* SLT2) k_sl_step_staged(GridI g, const float* __restrict__ v0,
+                                                               const float* __restrict__ v1,
+                                                               const float* __restrict__ u0, float* __restrict__ u1,
+                                                               float dt, float ih0, float ih1, float ih2, size_t N) {
+    using B = SLBox<CUBIC>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* S = (float4*)smem_raw;
+    const float ih[3] = {ih0, ih1, ih2};
+    const int o0 = blockIdx.z * SLT0, o1 = blockIdx.y * SLT1, o2 = blockIdx.x * SLT2;
+    const int i1 = o1 + threadIdx.x / SLT2, i2 = o2 + threadIdx.x % SLT2;
+    const int c0 = o0 - B::LO, c1 = o1 - B::LO, c2 = o2 - B::LO;  // box corner
+    const bool col = i1 < g.n1 && i2 < g.n2;
+    float disp[SLT0][3];
+    sl_stage<CUBIC>(S, v0, N, g, c0, c1, c2);
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < SLT0; ++p) {
+        const int i0 = o0 + p;
+        if (!col || i0 >= g.n0) continue;
+        const size_t x = ((size_t)i0 * g.n1 + i1) * g.n2 + i2;
+        float w1[3], d[3], vt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            w1[c] = v1[c * N + x];
+            d[c] = -dt * w1[c] * ih[c];
+        }
+        sl_interp<CUBIC>(S, v0, N, g, i0, i1, i2, c0, c1, c2, d, vt);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) disp[p][c] = -0.5f * dt * (w1[c] + vt[c]);
+    }
+    __syncthreads();
+    sl_stage<CUBIC>(S, u0, N, g, c0, c1, c2);
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < SLT0; ++p) {
+        const int i0 = o0 + p;
+        if (!col || i0 >= g.n0) continue;
+        const size_t x = ((size_t)i0 * g.n1 + i1) * g.n2 + i2;
+        float d[3], ut[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[c] = disp[p][c] * ih[c];
+        sl_interp<CUBIC>(S, u0, N, g, i0, i1, i2, c0, c1, c2, d, ut);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u1[c * N + x] = disp[p][c] + ut[c];
+    }
+}
+
 // m(x) = I(x + u(x))
 template <class T>
 __global__ void k_warp(GridI g, const T* __restrict__ img, const T* __restrict__ u, T* __restrict__ out, T ih0, T ih1,
