@@ -1,6 +1,8 @@
 // Pointwise kernels on real fields: the ad* / ad bilinear forms of the EPDiff
-// equation and of the Jacobi sweeps, semi-Lagrangian transport, warping,
-// Jacobian determinants and double-precision reductions.
+// equation and of the Jacobi sweeps, semi-Lagrangian transport (global-gather
+// and shared-memory-staged map steps), warping, the exact transposes of the
+// map step and of the warp (discrete gradient), Jacobian determinants and
+// double-precision reductions.
 //
 // A time state holds 24 real fields, each N = n0*n1*n2 values:
 //   [0..2]   v_c          [3 + 3c + j]  D_j v_c
