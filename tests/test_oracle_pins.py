@@ -571,3 +571,90 @@ def test_dealias_band_count_closed_form(n):
     assert int(g.band.sum()) == (2 * K[0] + 1) * (2 * K[1] + 1) * (K[2] + 1)
     for a in range(3):
         assert 2 * K[a] - n[a] < -K[a]  # the alias of the largest sum lies outside the band
+
+
+def _dense_operator(g, apply):
+    m = 3 * int(np.prod(g.n))
+    A = np.empty((m, m))
+    for j in range(m):
+        e = np.zeros(m)
+        e[j] = 1.0
+        A[:, j] = apply(e.reshape((3,) + g.n)).ravel()
+    return A
+
+
+def _krylov_galerkin_iterates(H, K, b, kmax):
+    """The PCG iterates characterised without the CG recurrence: x_k is the
+    Galerkin (H-orthogonal) projection of the solution of H x = b onto the
+    preconditioned Krylov space span{K b, (K H) K b, ..., (K H)^(k-1) K b}."""
+    xs, Q = [], np.zeros((b.size, 0))
+    v = K @ b
+    for _ in range(kmax):
+        for _ in range(2):
+            v = v - Q @ (Q.T @ v)
+        Q = np.hstack([Q, (v / np.linalg.norm(v))[:, None]])
+        xs.append(Q @ np.linalg.solve(Q.T @ H @ Q, Q.T @ b))
+        v = K @ (H @ Q[:, -1])
+    return xs
+
+
+def test_pcg_stopping_test_in_V_and_L2():
+    """PCG with preconditioner K stops at the first iteration whose residual,
+    measured in the norm of the chosen space (V: sqrt(<r, K r>); L2: ||r||),
+    is at most rtol times the initial one (reading C9 of the V / L2 variants
+    of Sec. 3).  The expected iteration and iterate come from the Galerkin
+    characterisation of PCG on the dense 4^3 Gauss-Newton Hessian; alpha = 1
+    makes K far from the identity, so the two norms stop at different
+    iterations for every rtol used here."""
+    n = (4, 4, 4)
+    g = O.Grid(n, alpha=1.0)
+    p = O.Params(alpha=1.0, nt=4, weight=1e-2)
+    r = synth.rng_for(70)
+    I0 = synth.spectral_gaussian_smooth(r.standard_normal(n), 0.6)
+    I1 = synth.spectral_gaussian_smooth(r.standard_normal(n), 0.6)
+    v0 = 0.3 * synth.spectral_gaussian_smooth(r.standard_normal(n), 0.6)[None] * np.array(
+        [1.0, -0.5, 0.8]).reshape(3, 1, 1, 1)
+    gl2, _, _, _, tr = O.gradient(g, p, v0, I0, I1)
+    H = _dense_hessian(g, p, tr)
+    K = _dense_operator(g, g.K)
+    b = -gl2.ravel()
+    xs = _krylov_galerkin_iterates(H, K, b, 8)
+    res = {"V": [math.sqrt(b @ K @ b)], "L2": [float(np.linalg.norm(b))]}
+    for x in xs:
+        rk = b - H @ x
+        res["V"].append(math.sqrt(rk @ K @ rk))
+        res["L2"].append(float(np.linalg.norm(rk)))
+    for rtol in (0.45, 0.105, 0.04):
+        want = {s: next(k for k in range(1, 9) if res[s][k] <= rtol * res[s][0]) for s in res}
+        assert want["V"] != want["L2"], (rtol, want)
+        for space in ("V", "L2"):
+            x, it = O.pcg(g, lambda d: O.hessvec(g, p, tr, d), -gl2, g.K, 20, rtol, space)
+            assert it == want[space], (rtol, space, it, want)
+            assert rel(x.ravel(), xs[it - 1]) < 1e-9
+
+
+def test_gauss_newton_armijo_acceptance():
+    """Each accepted Gauss-Newton step eps (update v0 <- v0 + eps x with
+    H x = -g, Sec. 3 with reading C1) satisfies the Armijo condition
+    E(v + eps x) <= E(v) + c1 eps <g, x>, recomputed here from the energy,
+    and, when eps < 1, the doubled step does not (halving from eps = 1).
+    c1 = 0.45 makes the condition decide: two of the four steps are halved."""
+    g = O.Grid((6, 6, 6), alpha=0.05)
+    p = O.Params(alpha=0.05, nt=4, weight=1e-3)
+    I0, vtrue = synth.blob_pair_inputs(g.n, 95, kmax=2, max_disp_vox=3.0)
+    I0 = synth.spectral_gaussian_smooth(I0, 1.0)
+    I1 = O.shoot(g, vtrue, p.nt, I0).m1
+    c1 = 0.45
+    rep = O.register(g, p, I0, I1, gn_maxit=4, pcg_maxit=8, c1=c1)
+    assert any(e < 1.0 for e in rep.steps) and any(e == 1.0 for e in rep.steps)
+    v = np.zeros((3,) + g.n)
+    for it, eps in zip(rep.pcg_iters, rep.steps):
+        gl2, E, _, _, tr = O.gradient(g, p, v, I0, I1)
+        x, _ = O.pcg(g, lambda d: O.hessvec(g, p, tr, d), -gl2, g.K, it, 0.0, force_iters=it)
+        slope = g.dot(gl2, x)
+        assert slope < 0.0
+        assert O.energy(g, p, v + eps * x, I0, I1)[0] <= E + c1 * eps * slope
+        if eps < 1.0:
+            assert O.energy(g, p, v + 2 * eps * x, I0, I1)[0] > E + c1 * 2 * eps * slope
+        v = v + eps * x
+    assert rel(v, rep.v0) < 1e-13
