@@ -32,8 +32,12 @@
  *    vectors).  A handle must not be used from two host threads at once.
  *  - No exception or abort crosses the ABI.  The first failure is sticky:
  *    later calls on the same handle return the same status until
- *    lddmm_destroy.  A NaN or Inf in a result is reported as
- *    LDDMM_ERR_NONFINITE by the calls that return an energy or a report.
+ *    lddmm_destroy.  Every call that takes device arrays first scans them
+ *    on the device (one extra launch over the inputs); a NaN or Inf there is
+ *    reported as LDDMM_ERR_NONFINITE by that call, which still enqueues its
+ *    work (its outputs are then undefined) and waits only for the scan's
+ *    verdict, not for the rest of its work.  A NaN or Inf in an energy or a
+ *    report gives the same status.  lddmm_apply_metric_noalloc does not scan.
  */
 #ifndef LDDMM_H
 #define LDDMM_H
@@ -51,7 +55,7 @@ typedef enum {
     LDDMM_ERR_OOM = 3,            /* device allocation failed                  */
     LDDMM_ERR_CUDA = 4,           /* a CUDA runtime call failed                */
     LDDMM_ERR_NOT_LINEARIZED = 5, /* hessvec / jacobi call before gradient     */
-    LDDMM_ERR_NONFINITE = 6,      /* NaN or Inf in an energy or a result       */
+    LDDMM_ERR_NONFINITE = 6,      /* NaN or Inf in an input, energy or result  */
     LDDMM_ERR_DEVICE_CHECK = 7,   /* a device-side check recorded an error     */
     LDDMM_ERR_TIMEOUT = 8,        /* a host-side wait exceeded its limit       */
     LDDMM_WARN_LINESEARCH = 9,    /* Armijo search failed; registration stopped */

@@ -101,7 +101,7 @@ const char* lddmm_status_string(lddmm_status s) {
         case LDDMM_ERR_OOM: return "device out of memory";
         case LDDMM_ERR_CUDA: return "CUDA runtime error";
         case LDDMM_ERR_NOT_LINEARIZED: return "no linearisation point: call lddmm_gradient first";
-        case LDDMM_ERR_NONFINITE: return "non-finite value in a result";
+        case LDDMM_ERR_NONFINITE: return "non-finite value in an input or a result";
         case LDDMM_ERR_DEVICE_CHECK: return "device-side or planner check failed";
         case LDDMM_ERR_TIMEOUT: return "host wait exceeded its limit";
         case LDDMM_WARN_LINESEARCH: return "Armijo line search failed; registration stopped early";

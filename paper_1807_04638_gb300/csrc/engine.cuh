@@ -27,6 +27,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -50,10 +51,12 @@ struct NvtxRange {
 };
 
 // Kernel classes for the optional CUDA-event profiler.
-enum KClass { KC_AX0 = 0, KC_AX1, KC_AX2, KC_ADSTAR, KC_TANPW, KC_ADJPW, KC_SL, KC_WARP, KC_RED, KC_SPEC, KC_MISC, KC_COUNT };
+enum KClass { KC_AX0 = 0, KC_AX1, KC_AX2, KC_ADSTAR, KC_TANPW, KC_ADJPW, KC_SL, KC_WARP, KC_RED, KC_SPEC, KC_MISC,
+              KC_SCAN, KC_COUNT };
 static const char* const kclass_names[KC_COUNT] = {
     "fft_axis0_c2c", "fft_axis1_c2c", "fft_axis2_r2c_c2r", "adstar_pointwise", "tangent_pointwise",
-    "adjoint_pointwise", "sl_map_step", "warp", "reduction", "spectral_combine", "misc_pointwise"};
+    "adjoint_pointwise", "sl_map_step", "warp", "reduction", "spectral_combine", "misc_pointwise",
+    "input_scan"};
 
 struct EngineBase {
     virtual ~EngineBase() {}
@@ -109,7 +112,42 @@ inline bool make_dims(const lddmm_grid* g, Dims* d) {
 
 constexpr int POOL = 48;   // partial spectra for the planner
 constexpr int RSCR = 42;   // real scratch fields
-constexpr int NSLOT = 64;  // device double result slots
+constexpr int NSLOT = 65;  // device double result slots
+constexpr int SCAN_SLOT = 64;  // verdict of the non-finite input scan
+
+// Pinned host result slots (NSLOT doubles per handle) from a process-wide
+// free list, so that creating or destroying a handle neither allocates nor
+// frees page-locked memory (either synchronises the whole device); they are
+// allocated 64 handles' worth at a time and never freed.
+inline std::mutex& pinned_mutex() {
+    static std::mutex m;
+    return m;
+}
+inline std::vector<double*>& pinned_free() {
+    static std::vector<double*> v;
+    return v;
+}
+inline double* pinned_slots_get() {
+    std::lock_guard<std::mutex> g(pinned_mutex());
+    std::vector<double*>& f = pinned_free();
+    if (f.empty()) {
+        constexpr int CHUNK = 64;
+        double* b = nullptr;
+        if (cudaMallocHost(&b, (size_t)CHUNK * NSLOT * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int i = CHUNK - 1; i >= 0; --i) f.push_back(b + (size_t)i * NSLOT);
+    }
+    double* p = f.back();
+    f.pop_back();
+    return p;
+}
+inline void pinned_slots_put(double* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(pinned_mutex());
+    pinned_free().push_back(p);
+}
 
 // Workspace layout (element counts).  Shared by the allocator and by
 // lddmm_workspace_bytes so admission control sees the true footprint.
@@ -145,6 +183,13 @@ inline Layout layout_for(const Dims& d, const lddmm_params* p, size_t tsize) {
 // axis; used to cross-check the register-blocked passes.
 inline bool force_generic_fft() {
     const char* e = getenv("LDDMM_GENERIC_FFT");
+    return e && e[0] == '1';
+}
+// LDDMM_SL_GATHER=1 makes the FP32 map steps use the global-gather kernel
+// k_sl_step instead of the shared-memory staged one; used to cross-check the
+// staged kernel, including its fallback for stencils that leave the box.
+inline bool force_sl_gather() {
+    const char* e = getenv("LDDMM_SL_GATHER");
     return e && e[0] == '1';
 }
 // LDDMM_FULL_BAND=1 transforms every spectral line even where the 2/3-rule
@@ -188,7 +233,9 @@ template <class K>
 inline bool raise_smem_limit(K kernel, size_t need) {
     const int mx = smem_optin_max();
     if ((size_t)mx < need) return false;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) == cudaSuccess;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) == cudaSuccess) return true;
+    cudaGetLastError();  // a refusal must not stay pending: the caller falls back to another kernel
+    return false;
 }
 
 // Grid of a persistent pass: `per_sm` resident blocks per SM, never more
@@ -335,6 +382,8 @@ class Engine : public EngineBase {
     bool exact_grad = false;
     T *px, *pr, *pz, *pp, *pq, *pg, *pvt;
     double *partial, *dres, *hres = nullptr;
+    cudaEvent_t scan_ev = nullptr;
+    bool scan_pending = false;
     FFTAxis ax[3];
     SpecTabs<T> tabs;
     int TLc[2], Pc[2], TL2, P2, Ph2;
@@ -433,8 +482,11 @@ class Engine : public EngineBase {
 
     ~Engine() override {
         for (auto& x : ev) cudaEventDestroy(x);
-        if (base_) cudaFree(base_);
-        if (hres) cudaFreeHost(hres);
+        if (scan_ev) cudaEventDestroy(scan_ev);
+        // stream-ordered: the workspace returns to the pool after the
+        // stream's queued work, with no device-wide synchronisation
+        if (base_) cudaFreeAsync(base_, st);
+        pinned_slots_put(hres);
     }
 
     lddmm_status fail(lddmm_status s) {
@@ -453,14 +505,19 @@ class Engine : public EngineBase {
     lddmm_status init() {
         Layout L = layout_for(d, &prm, sizeof(T));
         cap_ = L.bytes;
-        if (cudaMalloc(&base_, cap_) != cudaSuccess) {
+        // Set-up stays on the handle's stream (stream-ordered allocation,
+        // asynchronous fills and copies, one stream synchronisation), so that
+        // creating a handle does not wait for other handles' queued work.
+        if (cudaMallocAsync((void**)&base_, cap_, st) != cudaSuccess) {
             base_ = nullptr;
             cudaGetLastError();
             return fail(LDDMM_ERR_OOM);
         }
-        if (cudaMallocHost(&hres, NSLOT * sizeof(double)) != cudaSuccess) {
-            hres = nullptr;
-            return fail(LDDMM_ERR_OOM);
+        hres = pinned_slots_get();
+        if (!hres) return fail(LDDMM_ERR_OOM);
+        if (cudaEventCreateWithFlags(&scan_ev, cudaEventDisableTiming) != cudaSuccess) {
+            scan_ev = nullptr;
+            return fail(LDDMM_ERR_CUDA);
         }
         for (int i = 0; i < POOL; ++i) pool[i] = carve<C>(d.NS);
         for (int i = 0; i < 2; ++i) vhat[i] = carve<C>(3 * d.NS);
@@ -507,7 +564,8 @@ class Engine : public EngineBase {
         // LDDMM_POISON_WORKSPACE=1 fills the buffers with NaN bytes instead of
         // zeros, so that a test sees any read of an entry never written.
         const char* poison = getenv("LDDMM_POISON_WORKSPACE");
-        LD_CK(cudaMemset(base_, poison && poison[0] == '1' ? 0xFF : 0, off_));
+        LD_CK(cudaMemsetAsync(base_, poison && poison[0] == '1' ? 0xFF : 0, off_, st));
+        LD_CK(cudaMemsetAsync(dres + SCAN_SLOT, 0, sizeof(double), st));
         // twiddles and symbol tables
         const int ns[3] = {d.n0, d.n1, d.n2};
         for (int a = 0; a < 3; ++a) {
@@ -523,7 +581,8 @@ class Engine : public EngineBase {
                 tw[t].y = (T)sinl(ang);
             }
             C* dtw = carve<C>(n);
-            LD_CK(cudaMemcpy(dtw, tw.data(), n * sizeof(C), cudaMemcpyHostToDevice));
+            // pageable source: the call returns once the data is staged
+            LD_CK(cudaMemcpyAsync(dtw, tw.data(), n * sizeof(C), cudaMemcpyHostToDevice, st));
             ax[a].tw = dtw;
         }
         const int nk[3] = {d.n0, d.n1, d.n2h};
@@ -539,8 +598,8 @@ class Engine : public EngineBase {
             }
             T* ddk = carve<T>(nk[a]);
             T* dks = carve<T>(nk[a]);
-            LD_CK(cudaMemcpy(ddk, dk.data(), nk[a] * sizeof(T), cudaMemcpyHostToDevice));
-            LD_CK(cudaMemcpy(dks, ks.data(), nk[a] * sizeof(T), cudaMemcpyHostToDevice));
+            LD_CK(cudaMemcpyAsync(ddk, dk.data(), nk[a] * sizeof(T), cudaMemcpyHostToDevice, st));
+            LD_CK(cudaMemcpyAsync(dks, ks.data(), nk[a] * sizeof(T), cudaMemcpyHostToDevice, st));
             tabs.dk[a] = ddk;
             tabs.ksq[a] = dks;
         }
@@ -582,11 +641,11 @@ class Engine : public EngineBase {
         bs1 = (d.n1 - tabs.kcut[1]) & ~1;
         if (bc1 >= bs1) bc1 = bs1 = d.n1;
         if constexpr (sizeof(T) == 4)
-            sl_staged = raise_smem_limit(k_sl_step_staged<true>, SLBox<true>::SMEM) &&
+            sl_staged = !force_sl_gather() && raise_smem_limit(k_sl_step_staged<true>, SLBox<true>::SMEM) &&
                         raise_smem_limit(k_sl_step_staged<false>, SLBox<false>::SMEM);
         band_ok = prm.dealias && fast[0] && fast[1] && fast[2] && !force_full_band() &&
                   (bnb2 < d.n2h || bc1 < bs1);
-        LD_CK(cudaDeviceSynchronize());
+        LD_CK(cudaStreamSynchronize(st));
         return LDDMM_OK;
     }
 
@@ -1024,6 +1083,44 @@ class Engine : public EngineBase {
         return status;
     }
 
+    // Non-finite input scan (the error convention of the boundary): one
+    // launch over the array inputs of a call, whose verdict is copied to
+    // pinned host memory at once; scan_verdict() waits for that copy only
+    // (not for the call's other work, queued behind it) and makes
+    // LDDMM_ERR_NONFINITE sticky.
+    void scan_inputs(std::initializer_list<std::pair<const void*, size_t>> arrays) {
+        ScanArgs<T> a;
+        a.cnt = 0;
+        double bytes = 0.0;
+        for (const auto& x : arrays) {
+            if (!x.first || a.cnt == SCAN_MAX) continue;
+            a.p[a.cnt] = (const T*)x.first;
+            a.n[a.cnt] = x.second;
+            bytes += (double)x.second * sizeof(T);
+            a.cnt++;
+        }
+        if (!a.cnt) return;
+        {
+            PScope ps_(this, KC_SCAN, bytes);
+            k_nonfinite_scan<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, dres + SCAN_SLOT);
+        }
+        cudaMemcpyAsync(hres + SCAN_SLOT, dres + SCAN_SLOT, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaEventRecord(scan_ev, st);
+        scan_pending = true;
+    }
+    lddmm_status scan_verdict() {
+        if (!scan_pending) return status;
+        scan_pending = false;
+        if (cudaEventSynchronize(scan_ev) != cudaSuccess) return fail(LDDMM_ERR_CUDA);
+        if (hres[SCAN_SLOT] != 0.0) return fail(LDDMM_ERR_NONFINITE);
+        return status;
+    }
+    // end of an asynchronous call: launch errors, then the scan's verdict
+    lddmm_status finish() {
+        if (check_launch() != LDDMM_OK) return status;
+        return scan_verdict();
+    }
+
     // One semi-Lagrangian map step u0 -> u1 (velocities v0 at t_k, v1 at
     // t_{k+1}): the shared-memory staged kernel in FP32, the plain gather
     // kernel in FP64 (or if the staged kernel's shared memory was refused).
@@ -1452,6 +1549,7 @@ class Engine : public EngineBase {
     lddmm_status shoot(const void* v0, const void* I0, void* m1o, void* u1o, double* kinetic) override {
         if (status != LDDMM_OK) return status;
         if (!v0 || (m1o && !I0)) return fail(LDDMM_ERR_ARG);
+        scan_inputs({{v0, 3 * d.N}, {I0, d.N}});
         shoot_core((const T*)v0, kinetic != nullptr);
         lin_valid = false;
         if (I0) {
@@ -1461,7 +1559,7 @@ class Engine : public EngineBase {
             lin_valid = true;
         }
         if (u1o) cudaMemcpyAsync(u1o, u1(), 3 * d.N * sizeof(T), cudaMemcpyDeviceToDevice, st);
-        if (check_launch() != LDDMM_OK) return status;
+        if (finish() != LDDMM_OK) return status;
         if (kinetic) {
             if (fetch(0, prm.nt + 1) != LDDMM_OK) return status;
             for (int k = 0; k <= prm.nt; ++k) kinetic[k] = hres[k];
@@ -1472,8 +1570,9 @@ class Engine : public EngineBase {
     lddmm_status gradient(const void* v0, const void* I0, const void* I1, void* grad, double* energy) override {
         if (status != LDDMM_OK) return status;
         if (!v0 || !I0 || !I1 || !grad) return fail(LDDMM_ERR_ARG);
+        scan_inputs({{v0, 3 * d.N}, {I0, d.N}, {I1, d.N}});
         gradient_core((const T*)v0, (const T*)I0, (const T*)I1, (T*)grad, prm.space);
-        if (check_launch() != LDDMM_OK) return status;
+        if (finish() != LDDMM_OK) return status;
         if (energy) {
             if (fetch(0, prm.nt + 3) != LDDMM_OK) return status;
             const double data = hres[prm.nt + 2], reg = prm.weight * hres[prm.nt + 1];
@@ -1489,38 +1588,42 @@ class Engine : public EngineBase {
         if (status != LDDMM_OK) return status;
         if (!dv0 || !Hdv) return fail(LDDMM_ERR_ARG);
         if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
+        scan_inputs({{dv0, 3 * d.N}});
         hessvec_core((const T*)dv0, (T*)Hdv, prm.space);
-        return check_launch();
+        return finish();
     }
 
     lddmm_status jacobi_forward(const void* dv0, void* eta1, void* xi1) override {
         if (status != LDDMM_OK) return status;
         if (!dv0) return fail(LDDMM_ERR_ARG);
         if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
+        scan_inputs({{dv0, 3 * d.N}});
         fwd_vec((const T*)dv0, dhat);
         mask_copy(dhat, tan_[0]);
         cudaMemsetAsync(tan_[0] + 3 * d.NS, 0, 3 * d.NS * sizeof(C), st);
         tangent_sweep();
         if (eta1) inv_vec(tan_[prm.nt % 2], (T*)eta1, 3, true);
         if (xi1) inv_vec(tan_[prm.nt % 2] + 3 * d.NS, (T*)xi1, 3, true);
-        return check_launch();
+        return finish();
     }
 
     lddmm_status jacobi_adjoint(const void* beta, const void* bxi, void* out) override {
         if (status != LDDMM_OK) return status;
         if (!bxi || !out) return fail(LDDMM_ERR_ARG);
         if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
+        scan_inputs({{beta, 3 * d.N}, {bxi, 3 * d.N}});
         fwd_vec((const T*)bxi, adj[0] + 3 * d.NS, 1.0, 0, true);
         if (beta) fwd_vec((const T*)beta, adj[0], 1.0, 0, true);
         else cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
         adjoint_sweep();
         spec_to_real2(nullptr, sym(0.0, 0, -1), adj_result(), sym(1.0, 0, -1, 1), (T*)out);
-        return check_launch();
+        return finish();
     }
 
     lddmm_status apply_metric(const void* in, void* out, int ncomp, int power) override {
         if (status != LDDMM_OK) return status;
         if (!in || !out || ncomp < 1 || power < -4 || power > 4) return fail(LDDMM_ERR_ARG);
+        scan_inputs({{in, (size_t)ncomp * d.N}});
         for (int c0 = 0; c0 < ncomp; c0 += 3) {
             const int nc = std::min(3, ncomp - c0);
             std::vector<FwdOut> outs(nc);
@@ -1531,7 +1634,7 @@ class Engine : public EngineBase {
             forward(outs);
             inv_vec(tmp, (T*)out + (size_t)c0 * d.N, nc);
         }
-        return check_launch();
+        return finish();
     }
 
     void jacdet_into(const T* u, T* J) {
@@ -1556,15 +1659,17 @@ class Engine : public EngineBase {
     lddmm_status jacobian_det(const void* u, void* J, double* minmax) override {
         if (status != LDDMM_OK) return status;
         if (!u) return fail(LDDMM_ERR_ARG);
+        scan_inputs({{u, 3 * d.N}});
         T* Jd = J ? (T*)J : rs + 9 * d.N;
         jacdet_into((const T*)u, Jd);
+        if (minmax) minmax_async(Jd, d.N, 60);
+        if (finish() != LDDMM_OK) return status;
         if (minmax) {
-            minmax_async(Jd, d.N, 60);
             if (fetch(60, 3) != LDDMM_OK) return status;
             minmax[0] = hres[62];
             minmax[1] = hres[61];
         }
-        return check_launch();
+        return status;
     }
 
     // out = T^T (-G grad m1): the vector-Jacobian product of v0 -> m1 at the
@@ -1573,6 +1678,7 @@ class Engine : public EngineBase {
         if (status != LDDMM_OK) return status;
         if (!G || !out) return fail(LDDMM_ERR_ARG);
         if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
+        scan_inputs({{G, d.N}});
         {
             PScope ps_(this, KC_MISC, 8.0 * d.N * sizeof(T));
             k_vjp_source<T><<<pw_grid(d.N), PW_THREADS, 0, st>>>((const T*)G, gm1, rs, d.N);
@@ -1581,7 +1687,7 @@ class Engine : public EngineBase {
         cudaMemsetAsync(adj[0], 0, 3 * d.NS * sizeof(C), st);
         adjoint_sweep();
         spec_to_real2(nullptr, sym(0.0, 0, -1), adj_result(), sym(1.0, 0, -1, 1), (T*)out);
-        return check_launch();
+        return finish();
     }
 
     lddmm_status synchronize() override {
@@ -1617,6 +1723,8 @@ class Engine : public EngineBase {
     lddmm_status reg(const void* I0v, const void* I1v, void* v0v, lddmm_report* rep) override {
         if (status != LDDMM_OK) return status;
         if (!I0v || !I1v || !v0v) return fail(LDDMM_ERR_ARG);
+        scan_inputs({{I0v, d.N}, {I1v, d.N}, {v0v, 3 * d.N}});
+        if (scan_verdict() != LDDMM_OK) return status;
         const T* I0 = (const T*)I0v;
         const T* I1 = (const T*)I1v;
         T* v = (T*)v0v;

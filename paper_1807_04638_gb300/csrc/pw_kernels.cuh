@@ -614,6 +614,25 @@ __global__ void k_absmax_partial(const T* __restrict__ a, size_t n, double* __re
     }
 }
 
+// Non-finite scan of up to SCAN_MAX arrays: *flag = 1 when any entry is a
+// NaN or an infinity (the flag is never cleared; the caller's status is
+// sticky).  The result does not depend on the launch shape.
+constexpr int SCAN_MAX = 4;
+template <class T> struct ScanArgs {
+    const T* p[SCAN_MAX];
+    size_t n[SCAN_MAX];
+    int cnt;
+};
+template <class T>
+__global__ void k_nonfinite_scan(const __grid_constant__ ScanArgs<T> a, double* __restrict__ flag) {
+    bool bad = false;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int i = 0; i < a.cnt; ++i)
+        for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < a.n[i]; x += stride)
+            bad |= !isfinite(a.p[i][x]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) *flag = 1.0;
+}
+
 // out[slot] = scale * reduce(partial[0..nb*stride) with the given stride/offset)
 static __global__ void k_finish(const double* __restrict__ partial, int nb, int stride, int off, int op, double scale,
                          double* __restrict__ out) {

@@ -57,11 +57,21 @@ def _key(n, p: N.lddmm_params, lengths):
     return (tuple(n), tuple(lengths) if lengths else None) + tuple(getattr(p, f) for f, _ in p._fields_)
 
 
+@dataclasses.dataclass
+class Reservation:
+    """Bytes counted against the budget for a handle not created yet, and the
+    parked handles evicted to make room, which the caller closes (outside the
+    server's lock, since closing and creating handles call into CUDA)."""
+    need: int
+    victims: List[object]
+
+
 class HandlePool:
     """HBM-budget accounting of the live handles of a server: the ones in
     use and the ones parked for reuse by a later request with the same key
     (grid and parameters).  A handle is a pair (object with close(), bytes).
-    The pool itself takes no lock; the server calls it under its own."""
+    The pool itself takes no lock; the server calls it under its own, and
+    creates and closes handles outside it."""
 
     def __init__(self, budget_bytes: float):
         self.budget = float(budget_bytes)
@@ -69,12 +79,11 @@ class HandlePool:
         self.peak_used = 0.0
         self.parked: Dict[tuple, List[Tuple[object, int]]] = {}
 
-    def acquire(self, key, need: int, make):
-        """A parked handle of `key`, else a new one from make() once `need`
-        bytes fit the budget, closing parked handles of other keys to make
-        room.  Returns (handle, bytes); None when the request must wait for
-        handles in use to be released; raises ValueError when it can never
-        fit."""
+    def reserve(self, key, need: int):
+        """A parked handle of `key` as (handle, bytes), else a Reservation of
+        `need` bytes once they fit the budget, evicting parked handles of
+        other keys to make room.  None when the request must wait for handles
+        in use to be released; raises ValueError when it can never fit."""
         pool = self.parked.get(key)
         if pool:
             return pool.pop()
@@ -82,25 +91,49 @@ class HandlePool:
             raise ValueError("invalid request shape or parameters")
         if need > self.budget:
             raise ValueError(f"exceeds the HBM budget ({need / 1e9:.1f} GB > {self.budget / 1e9:.1f} GB)")
+        evicted = []  # (key, handle, bytes)
         while self.used + need > self.budget:
             victim = next((kk for kk, v in self.parked.items() if v), None)
             if victim is None:
+                # not enough room yet: the evicted handles stay parked
+                for kk, h, b in evicted:
+                    self.parked[kk].append((h, b))
+                    self.used += b
                 return None
             h, b = self.parked[victim].pop()
-            h.close()
+            evicted.append((victim, h, b))
             self.used -= b
-        h = make()
         self.used += need
         self.peak_used = max(self.peak_used, self.used)
-        return h, need
+        return Reservation(need, [h for _, h, _ in evicted])
+
+    def cancel(self, r: Reservation):
+        """The handle of a reservation could not be created."""
+        self.used -= r.need
+
+    def acquire(self, key, need: int, make):
+        """reserve(), then close the evicted handles and create the new one
+        with make() in the caller's thread.  Returns (handle, bytes) or None;
+        raises ValueError when the request can never fit."""
+        r = self.reserve(key, need)
+        if not isinstance(r, Reservation):
+            return r
+        for h in r.victims:
+            h.close()
+        try:
+            return make(), r.need
+        except Exception:
+            self.cancel(r)
+            raise
 
     def park(self, key, hb):
         self.parked.setdefault(key, []).append(hb)
 
     def drop(self, hb):
-        """Close a handle that is not to be reused (its request failed)."""
-        hb[0].close()
+        """Forget a handle that is not to be reused (its request failed); the
+        caller closes it."""
         self.used -= hb[1]
+        return hb[0]
 
     def close_parked(self):
         for pool in self.parked.values():
@@ -131,17 +164,19 @@ class Server:
         return self.pool.peak_used
 
     # -- memory accounting ------------------------------------------------------
-    def _acquire_handle(self, req: Request) -> Optional[Tuple[N.Handle, int]]:
-        """Called with the lock held; returns a handle or None if it must wait."""
+    def _reserve_handle(self, req: Request):
+        """Called with the lock held: a parked handle, a Reservation, or None
+        if the request must wait."""
         n = req.I0.shape
         k = _key(n, req.params, req.lengths)
+        return self.pool.reserve(k, N.workspace_bytes(n, req.params, req.lengths))
 
-        def make():
-            with self.torch.cuda.device(self.device):
-                stream = self.torch.cuda.Stream(device=self.device)
-                return N.Handle(n, req.params, lengths=req.lengths, stream=stream, device=self.device.index)
-
-        return self.pool.acquire(k, N.workspace_bytes(n, req.params, req.lengths), make)
+    def _make_handle(self, req: Request) -> N.Handle:
+        """Called without the lock (from the request's worker thread)."""
+        with self.torch.cuda.device(self.device):
+            stream = self.torch.cuda.Stream(device=self.device)
+            return N.Handle(req.I0.shape, req.params, lengths=req.lengths, stream=stream,
+                            device=self.device.index)
 
     def _release_handle(self, req: Request, hb):
         self.pool.park(_key(req.I0.shape, req.params, req.lengths), hb)
@@ -149,8 +184,23 @@ class Server:
     # -- request execution ------------------------------------------------------
     def _run(self, req: Request, hb):
         torch = self.torch
-        h, _ = hb
         res = self.results[req.rid]
+        if isinstance(hb, Reservation):
+            # evict and create outside the lock: other requests keep running
+            # and releasing their handles meanwhile
+            try:
+                for victim in hb.victims:
+                    victim.close()
+                hb = (self._make_handle(req), hb.need)
+            except Exception as e:
+                res.status = f"error: {e}"
+                res.finished = time.perf_counter() - self.t0
+                with self.lock:
+                    self.pool.cancel(hb)
+                    self.inflight -= 1
+                    self.lock.notify_all()
+                return
+        h, _ = hb
         try:
             dt = h.dtype
             if not (np.isfinite(req.I0).all() and np.isfinite(req.I1).all()):
@@ -168,8 +218,10 @@ class Server:
         finally:
             res.finished = time.perf_counter() - self.t0
             sticky = N.lib().lddmm_last_status(h._h) if h._h else 0
+            if sticky != 0:  # a failed handle is not reused; closed outside the lock
+                h.close()
             with self.lock:
-                if sticky != 0:  # a failed handle is not reused
+                if sticky != 0:
                     self.pool.drop(hb)
                 else:
                     self._release_handle(req, hb)
@@ -195,7 +247,7 @@ class Server:
                         r.status, r.finished = "error: admission deadline exceeded", now
                         continue
                     try:
-                        hb = self._acquire_handle(req)
+                        hb = self._reserve_handle(req)
                     except Exception as e:
                         backlog.pop(0)
                         r = self.results[req.rid]

@@ -338,6 +338,110 @@ def test_degenerate_cases(pkg, prec, n):
         assert rel(host(e1), g.P(d)) < tol and rel(host(x1), g.P(d)) < tol
 
 
+MAP_STEP_CASES = [
+    # (grid, constant velocity in voxels over unit time, peak of the random part)
+    ((12, 10, 15), (0.0, 0.0, 2.0), 2.0),   # the staged box wraps onto itself
+    ((32, 32, 32), (0.0, 0.0, 1.0), 4.0),   # about a quarter of the points leave the box
+    ((32, 32, 32), (2.0, -2.0, 2.0), 3.0),  # nearly every point leaves the box
+]
+
+
+@pytest.mark.parametrize("interp", ["cubic", "linear"])
+@pytest.mark.parametrize("n,shift,peak", MAP_STEP_CASES)
+def test_map_step_beyond_staged_box(pkg, interp, n, shift, peak, monkeypatch):
+    """Semi-Lagrangian map steps (Sec. 3 state equation, reading C6) whose
+    departure points lie more than one voxel away: the FP32 staged kernel
+    takes its global-gather fallback for those stencils and its shared-memory
+    taps for the others, within one block.  Its maps equal those of the plain
+    gather kernel (LDDMM_SL_GATHER=1) bit for bit, and both match the oracle;
+    the FP64 engine (gather kernel) matches it to 1e-10."""
+    nt = 2
+    g = O.Grid(n, alpha=0.01)
+    I0 = synth.spectral_gaussian_smooth(synth.blob_phantom(n, synth.rng_for(93)), 1.0)
+    v0 = synth.random_velocity(n, synth.rng_for(94), 2, peak) + np.stack(
+        [np.full(n, shift[a] * g.h[a]) for a in range(3)])
+    # departure displacement of the first step, in voxels: some stencils leave
+    # the staged box (|d| > 1), others stay inside it
+    d = np.abs(v0 / nt / np.array(g.h).reshape(3, 1, 1, 1)).max(axis=0)
+    assert (d > 1.25).any() and (d < 0.9).any() or (d > 1.25).mean() > 0.5
+    tr = O.shoot(g, v0, nt, I0, kind=interp)
+    code = pkg.LDDMM_INTERP_CUBIC if interp == "cubic" else pkg.LDDMM_INTERP_LINEAR
+    out = {}
+    for mode in ("staged", "gather"):
+        if mode == "gather":
+            monkeypatch.setenv("LDDMM_SL_GATHER", "1")
+        else:
+            monkeypatch.delenv("LDDMM_SL_GATHER", raising=False)
+        with pkg.Handle(n, params(pkg, "f32", nt=nt, interp=code)) as h:
+            m1, u1 = h.new_img(), h.new_vec()
+            h.lddmm_shoot(dev(v0, torch.float32), dev(I0, torch.float32), m1, u1)
+            h.lddmm_synchronize()
+            out[mode] = (u1.clone(), m1.clone())
+    monkeypatch.delenv("LDDMM_SL_GATHER", raising=False)
+    assert torch.equal(out["staged"][0], out["gather"][0])
+    assert torch.equal(out["staged"][1], out["gather"][1])
+    assert rel(host(out["staged"][0]), tr.u) < 1e-5
+    assert rel(host(out["staged"][1]), tr.m1) < 1e-5
+    with pkg.Handle(n, params(pkg, "f64", nt=nt, interp=code)) as h:
+        m1, u1 = h.new_img(), h.new_vec()
+        h.lddmm_shoot(dev(v0, torch.float64), dev(I0, torch.float64), m1, u1)
+        h.lddmm_synchronize()
+        assert rel(host(u1), tr.u) < F64_TOL
+        assert rel(host(m1), tr.m1) < F64_TOL
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_nonfinite_inputs_are_reported(pkg, prec):
+    """A NaN or an infinity in any array input is found by the device scan
+    and returned as LDDMM_ERR_NONFINITE (6) by the call that received it; the
+    status is then sticky on the handle.  Clean inputs leave it at 0."""
+    dtype, _ = DT[prec]
+    n = (12, 10, 15)
+    nt = 2
+    g, I0, I1, vtrue = problem(n, 3, nt)
+    v0 = 0.5 * vtrue
+    bad = np.zeros((3,) + n)
+    bad[1, 3, 4, 5] = np.nan
+    badimg = I1.copy()
+    badimg[2, 0, 7] = np.inf
+
+    def linearised():
+        h = pkg.Handle(n, params(pkg, prec, nt=nt))
+        h.lddmm_gradient(dev(v0, dtype), dev(I0, dtype), dev(I1, dtype), h.new_vec())
+        return h
+
+    calls = [
+        ("hessvec", lambda h: h.lddmm_hessvec(dev(bad, dtype), h.new_vec())),
+        ("jacobi_forward", lambda h: h.lddmm_jacobi_forward(dev(bad, dtype), h.new_vec(), h.new_vec())),
+        ("jacobi_adjoint", lambda h: h.lddmm_jacobi_adjoint(None, dev(bad, dtype), h.new_vec())),
+        ("shoot_vjp", lambda h: h.lddmm_shoot_vjp(dev(badimg, dtype), h.new_vec())),
+        ("shoot", lambda h: h.lddmm_shoot(dev(bad + v0, dtype), dev(I0, dtype), h.new_img())),
+        ("gradient", lambda h: h.lddmm_gradient(dev(v0, dtype), dev(I0, dtype), dev(badimg, dtype), h.new_vec())),
+        ("apply_metric", lambda h: h.lddmm_apply_metric(dev(bad, dtype), h.new_vec(), -1)),
+        ("jacobian_det", lambda h: h.lddmm_jacobian_det(dev(bad, dtype))),
+        ("register", lambda h: h.lddmm_register(dev(I0, dtype), dev(badimg, dtype), dev(np.zeros((3,) + n), dtype))),
+    ]
+    for name, call in calls:
+        with linearised() as h:
+            assert pkg.lib().lddmm_last_status(h._h) == 0, name
+            with pytest.raises(pkg.LddmmError) as ei:
+                call(h)
+                h.lddmm_synchronize()
+            assert ei.value.status == 6, (name, ei.value.status)
+            # sticky: a clean call on the same handle reports it again
+            with pytest.raises(pkg.LddmmError) as ei:
+                h.lddmm_hessvec(dev(v0, dtype), h.new_vec())
+            assert ei.value.status == 6, name
+    # clean inputs: no false alarm, also after a run of calls
+    with linearised() as h:
+        out = h.new_vec()
+        for _ in range(3):
+            h.lddmm_hessvec(dev(v0, dtype), out)
+        h.lddmm_apply_metric(dev(v0, dtype), out, 1)
+        h.lddmm_synchronize()
+        assert pkg.lib().lddmm_last_status(h._h) == 0
+
+
 def test_errors_are_reported(pkg):
     n = (8, 8, 8)
     with pytest.raises(pkg.LddmmError):

@@ -2,7 +2,7 @@
 (serve.HandlePool), with fake handles in place of device workspaces."""
 import pytest
 
-from paper_1807_04638_gb300.serve import HandlePool
+from paper_1807_04638_gb300.serve import HandlePool, Reservation
 
 
 class Fake:
@@ -55,9 +55,43 @@ def test_failed_handles_are_dropped_and_parked_ones_closed_at_the_end():
     pool = HandlePool(100)
     a = pool.acquire("A", 30, lambda: Fake("a"))
     b = pool.acquire("B", 30, lambda: Fake("b"))
-    pool.drop(a)
-    assert a[0].closed and pool.used == 30
+    assert pool.drop(a) is a[0] and not a[0].closed   # the caller closes it
+    assert pool.used == 30
     pool.park("B", b)
     pool.close_parked()
     assert b[0].closed and pool.used == 0 and not pool.parked
     assert pool.peak_used == 60
+
+
+def test_reservation_counts_bytes_before_the_handle_exists():
+    """The server reserves bytes under its lock and creates the handle (and
+    closes evicted ones) outside it: the reservation already counts against
+    the budget, eviction is undone when room cannot be made, and a failed
+    creation gives the bytes back."""
+    pool = HandlePool(100)
+    a = pool.acquire("A", 50, lambda: Fake("a"))
+    pool.park("A", a)
+    b = pool.acquire("B", 40, lambda: Fake("b"))          # in use
+    r = pool.reserve("C", 60)                               # needs A's room
+    assert isinstance(r, Reservation) and r.victims == [a[0]] and not a[0].closed
+    assert pool.used == 100 and not pool.parked["A"]
+    # nothing else can be admitted while the reservation holds its bytes
+    assert pool.reserve("D", 10) is None
+    pool.cancel(r)
+    assert pool.used == 40
+    # no room even after evicting every parked handle: the parked one stays
+    pool.park("B", b)
+    c = pool.acquire("C", 50, lambda: Fake("c"))
+    assert pool.reserve("E", 60) is None
+    assert pool.parked["B"] == [b] and pool.used == 90
+
+
+def test_failed_creation_releases_the_reservation():
+    pool = HandlePool(100)
+
+    def boom():
+        raise RuntimeError("device out of memory")
+
+    with pytest.raises(RuntimeError):
+        pool.acquire("A", 70, boom)
+    assert pool.used == 0
