@@ -35,6 +35,7 @@
 #include "common.cuh"
 #include "fft_fast.cuh"
 #include "fft_kernels.cuh"
+#include "fused_stage.cuh"
 #include "lddmm.h"
 #include "pw_kernels.cuh"
 
@@ -52,11 +53,11 @@ struct NvtxRange {
 
 // Kernel classes for the optional CUDA-event profiler.
 enum KClass { KC_AX0 = 0, KC_AX1, KC_AX2, KC_ADSTAR, KC_TANPW, KC_ADJPW, KC_SL, KC_WARP, KC_RED, KC_SPEC, KC_MISC,
-              KC_SCAN, KC_COUNT };
+              KC_SCAN, KC_TANF, KC_ADJF, KC_COUNT };
 static const char* const kclass_names[KC_COUNT] = {
     "fft_axis0_c2c", "fft_axis1_c2c", "fft_axis2_r2c_c2r", "adstar_pointwise", "tangent_pointwise",
     "adjoint_pointwise", "sl_map_step", "warp", "reduction", "spectral_combine", "misc_pointwise",
-    "input_scan"};
+    "input_scan", "tangent_stage_fused", "adjoint_stage_fused"};
 
 struct EngineBase {
     virtual ~EngineBase() {}
@@ -110,7 +111,7 @@ inline bool make_dims(const lddmm_grid* g, Dims* d) {
     return true;
 }
 
-constexpr int POOL = 48;   // partial spectra for the planner
+constexpr int POOL = 64;   // partial spectra for the planner (a fused stage holds 57)
 constexpr int RSCR = 42;   // real scratch fields
 constexpr int NSLOT = 65;  // device double result slots
 constexpr int SCAN_SLOT = 64;  // verdict of the non-finite input scan
@@ -190,6 +191,12 @@ inline bool force_generic_fft() {
 // staged kernel, including its fallback for stencils that leave the box.
 inline bool force_sl_gather() {
     const char* e = getenv("LDDMM_SL_GATHER");
+    return e && e[0] == '1';
+}
+// LDDMM_UNFUSED=1 runs the Jacobi stages as separate axis-2 passes and
+// pointwise kernels instead of the fused stage kernels (cross-check).
+inline bool force_unfused() {
+    const char* e = getenv("LDDMM_UNFUSED");
     return e && e[0] == '1';
 }
 // LDDMM_FULL_BAND=1 transforms every spectral line even where the 2/3-rule
@@ -330,6 +337,32 @@ template <class T> struct FastPass {
     static bool has(int n) { return n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 192 || n == 256; }
 };
 
+// Launch of the fused Jacobi stage kernels (FP32, n2 with an E = 8 plan).
+struct FusedPass {
+    static bool has(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
+    static int tile_rows(int n) { return FAST_THREADS / (n / 8); }
+    template <int N, class SS, int KIND> static bool go(const FusedArgs& a, cudaStream_t st, bool set_attr) {
+        constexpr size_t sm = KIND == 0 ? FusedGeom<N>::SMEM0 : FusedGeom<N>::SMEM1;
+        if (set_attr) return raise_smem_limit(k_fused_stage<SS, N, KIND>, sm);
+        k_fused_stage<SS, N, KIND><<<persistent_grid(a.ntiles, FUSED_BLOCKS), FAST_THREADS, sm, st>>>(a);
+        return true;
+    }
+    template <class SS, int KIND>
+    static bool launch(int n, const FusedArgs& a, cudaStream_t st, bool set_attr = false) {
+        switch (n) {
+            case 32: return go<32, SS, KIND>(a, st, set_attr);
+            case 64: return go<64, SS, KIND>(a, st, set_attr);
+            case 128: return go<128, SS, KIND>(a, st, set_attr);
+            case 256: return go<256, SS, KIND>(a, st, set_attr);
+            default: return false;
+        }
+    }
+    static bool prepare(int n) {
+        return launch<float, 0>(n, FusedArgs{}, 0, true) && launch<float, 1>(n, FusedArgs{}, 0, true) &&
+               launch<__nv_bfloat16, 0>(n, FusedArgs{}, 0, true) && launch<__nv_bfloat16, 1>(n, FusedArgs{}, 0, true);
+    }
+};
+
 #define LD_CK(call)                                           \
     do {                                                      \
         cudaError_t e_ = (call);                              \
@@ -391,6 +424,7 @@ class Engine : public EngineBase {
     // band-limited transforms (all three passes register-blocked, dealiasing on)
     bool band_ok = false;
     bool sl_staged = false;  // FP32 map steps use k_sl_step_staged
+    bool fused = false;      // FP32 Jacobi stages use k_fused_stage
     int bnb2 = 0, bc1 = 0, bs1 = 0;
     size_t smem_c[2], smem2;
     int pool_top = 0;
@@ -645,6 +679,9 @@ class Engine : public EngineBase {
                         raise_smem_limit(k_sl_step_staged<false>, SLBox<false>::SMEM);
         band_ok = prm.dealias && fast[0] && fast[1] && fast[2] && !force_full_band() &&
                   (bnb2 < d.n2h || bc1 < bs1);
+        if constexpr (sizeof(T) == 4)
+            fused = band_ok && !force_unfused() && FusedPass::has(d.n2) &&
+                    d.rows % (size_t)FusedPass::tile_rows(d.n2) == 0 && FusedPass::prepare(d.n2);
         LD_CK(cudaStreamSynchronize(st));
         return LDDMM_OK;
     }
@@ -772,10 +809,49 @@ class Engine : public EngineBase {
         dot_async(lv0, v0, 3 * d.N, slot, d.cell);
     }
 
+    // The axis-2 inputs of an inverse transform: request r reads spectrum
+    // k1[r1[r]] (after the axis-0 and axis-1 passes), with i kappa_2 applied
+    // when d2[r].
+    struct InvHead {
+        std::vector<C*> k1;
+        std::vector<int> r1;
+        std::vector<char> d2;
+        bool bd;
+    };
+
     // real_out = F^-1[ sym . lincomb(src) ]
     // band: every source is band-limited or every request is masked, so the
     // transform may read the band only (the requests then all carry P).
-    void inverse(const std::vector<SpecLin>& srcs, const std::vector<InvReq>& reqs_in, bool band = false) {
+    void inverse(const std::vector<SpecLin>& srcs, const std::vector<InvReq>& reqs, bool band = false) {
+        const InvHead ih = inverse_head(srcs, reqs, band);
+        std::vector<PassJob> jobs;
+        for (size_t i1 = 0; i1 < ih.k1.size(); ++i1) {
+            PassJob j = blank();
+            auto setin = [&]() {
+                j.nin = 1;
+                j.in[0] = ih.k1[i1];
+                j.isym[0] = sym(1.0, 0, -1);
+            };
+            setin();
+            for (size_t r = 0; r < reqs.size(); ++r) {
+                if (ih.r1[r] != (int)i1) continue;
+                if (j.nout == MAXO) {
+                    jobs.push_back(j);
+                    j = blank();
+                    setin();
+                }
+                j.out[j.nout] = reqs[r].out;
+                j.osym[j.nout] = sym(1.0, 0, ih.d2[r] ? 2 : -1);
+                j.nout++;
+            }
+            if (j.nout) jobs.push_back(j);
+        }
+        launch(2, +1, jobs, ih.bd);
+    }
+
+    // The axis-0 and axis-1 passes of inverse(), with the fan-out shared as a
+    // tree; the pool's partial spectra hold the results.
+    InvHead inverse_head(const std::vector<SpecLin>& srcs, const std::vector<InvReq>& reqs_in, bool band) {
         const bool bd = band && band_ok;
         std::vector<InvReq> reqs = reqs_in;
         if (bd)
@@ -868,35 +944,27 @@ class Engine : public EngineBase {
             if (j.nout) jobs.push_back(j);
         }
         launch(1, +1, jobs, bd);
-        // axis 2
-        jobs.clear();
-        for (size_t i1 = 0; i1 < k1s.size(); ++i1) {
-            PassJob j = blank();
-            auto setin = [&]() {
-                j.nin = 1;
-                j.in[0] = k1s[i1].buf;
-                j.isym[0] = sym(1.0, 0, -1);
-            };
-            setin();
-            for (size_t r = 0; r < reqs.size(); ++r) {
-                if (r1[r] != (int)i1) continue;
-                if (j.nout == MAXO) {
-                    jobs.push_back(j);
-                    j = blank();
-                    setin();
-                }
-                j.out[j.nout] = reqs[r].out;
-                j.osym[j.nout] = sym(1.0, 0, reqs[r].sym.deriv == 2 ? 2 : -1);
-                j.nout++;
-            }
-            if (j.nout) jobs.push_back(j);
-        }
-        launch(2, +1, jobs, bd);
+        InvHead ih;
+        ih.bd = bd;
+        for (const K1& k : k1s) ih.k1.push_back(k.buf);
+        ih.r1 = r1;
+        for (const InvReq& q : reqs) ih.d2.push_back(q.sym.deriv == 2);
+        return ih;
     }
 
     // spec_out = sum bases + sum_i sym_i . F(real_i)
     // band: only the band of the output is ever used (it is masked, or every
     // consumer applies P), so the transform writes the band only, with P.
+    // An axis-2 output of a forward transform: the partial spectrum of the
+    // terms of output o with the same (lpow, scale, mask) whose derivative is
+    // along axis 0 (cls 0), axis 1 (cls 1), or axis 2 / none (cls 2).
+    struct G {
+        int o, lpow;
+        double scale;
+        int cls, mask;
+        C* buf;
+        int nin;
+    };
     void forward(const std::vector<FwdOut>& outs_in, bool band = false) {
         const bool bd = band && band_ok;
         std::vector<FwdOut> outs = outs_in;
@@ -904,13 +972,6 @@ class Engine : public EngineBase {
             for (FwdOut& o : outs)
                 for (FwdTerm& t : o.terms) t.sym.mask = 1;
         pool_top = 0;
-        struct G {
-            int o, lpow;
-            double scale;
-            int cls, mask;
-            C* buf;
-            int nin;
-        };
         // axis 2
         std::vector<G> g2;
         std::vector<PassJob> j2;
@@ -938,6 +999,11 @@ class Engine : public EngineBase {
             }
         }
         launch(2, -1, j2, bd);
+        forward_tail(outs, g2, bd);
+    }
+
+    // The axis-1 and axis-0 passes of forward(), from its axis-2 outputs g2.
+    void forward_tail(const std::vector<FwdOut>& outs, const std::vector<G>& g2, bool bd) {
         // axis 1
         std::vector<G> g1;
         std::vector<PassJob> j1;
@@ -1309,16 +1375,6 @@ class Engine : public EngineBase {
                     reqs.push_back({3 + c, sym(1.0, 0, -1), X + c * d.N});
                     for (int j = 0; j < 3; ++j) reqs.push_back({3 + c, sym(1.0, 0, j), X + (3 + 3 * c + j) * d.N});
                 }
-                inverse(srcs, reqs, true);
-                {
-                    PScope ps_(this, KC_TANPW, 24.0 * d.N * state_elem() + 42.0 * d.N * sizeof(T));
-                    if (bf16)
-                        k_tangent_pw<T, __nv_bfloat16><<<pw_grid(d.N), PW_THREADS, 0, st>>>(
-                            StatePtr<__nv_bfloat16>{state_bf(sidx), d.N}, StatePtr<T>{E, d.N}, X, pq_, d.N);
-                    else
-                        k_tangent_pw<T, T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{state(sidx), d.N},
-                                                                               StatePtr<T>{E, d.N}, X, pq_, d.N);
-                }
                 std::vector<FwdOut> outs(6);
                 for (int c = 0; c < 3; ++c) {
                     FwdOut& oe = outs[c];
@@ -1342,9 +1398,110 @@ class Engine : public EngineBase {
                         ox.bases.push_back({be + c * d.NS, 0.5 * dt_ * dt_});
                     }
                 }
+                if (fused) {
+                    tangent_stage_fused(srcs, reqs, outs, sidx);
+                    continue;
+                }
+                inverse(srcs, reqs, true);
+                {
+                    PScope ps_(this, KC_TANPW, 24.0 * d.N * state_elem() + 42.0 * d.N * sizeof(T));
+                    if (bf16)
+                        k_tangent_pw<T, __nv_bfloat16><<<pw_grid(d.N), PW_THREADS, 0, st>>>(
+                            StatePtr<__nv_bfloat16>{state_bf(sidx), d.N}, StatePtr<T>{E, d.N}, X, pq_, d.N);
+                    else
+                        k_tangent_pw<T, T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{state(sidx), d.N},
+                                                                               StatePtr<T>{E, d.N}, X, pq_, d.N);
+                }
                 forward(outs, true);
             }
         }
+    }
+
+    // ---- fused Jacobi stages (FP32): axis-0/1 passes of the inverse transform,
+    // one fused kernel (axis-2 inverse, pointwise products, axis-2 forward),
+    // axis-1/0 passes of the forward transform
+    void fused_launch(FusedArgs& a, int sidx, int kind) {
+        if constexpr (sizeof(T) == 4) {
+            a.states = bf16 ? (const void*)state_bf(sidx) : (const void*)state(sidx);
+            a.dk2 = (const float*)tabs.dk[2];
+            a.tw = (const cpx<float>*)ax[2].tw;
+            a.rows = (int)d.rows;
+            a.nb2 = bnb2;
+            a.ntiles = (int)(d.rows / (size_t)FusedPass::tile_rows(d.n2));
+            a.npts = (unsigned)d.N;
+            const double band = (double)bnb2 * d.rows * sizeof(C);
+            const double bytes = 33.0 * band + 24.0 * d.N * state_elem() + (a.eta_src ? 3.0 * d.N * sizeof(T) : 0.0);
+            PScope ps_(this, kind == 0 ? KC_TANF : KC_ADJF, bytes);
+            if (bf16) {
+                if (kind == 0) FusedPass::launch<__nv_bfloat16, 0>(d.n2, a, st);
+                else FusedPass::launch<__nv_bfloat16, 1>(d.n2, a, st);
+            } else {
+                if (kind == 0) FusedPass::launch<float, 0>(d.n2, a, st);
+                else FusedPass::launch<float, 1>(d.n2, a, st);
+            }
+        }
+    }
+    // tangent stage: requests per component c (12 c + ...): eta, D_j eta (3),
+    // mu, D_j mu (3), xi, D_j xi (3); outputs p_0..2, q_0..2
+    void tangent_stage_fused(const std::vector<SpecLin>& srcs, const std::vector<InvReq>& reqs,
+                             const std::vector<FwdOut>& outs, int sidx) {
+        const InvHead ih = inverse_head(srcs, reqs, true);
+        FusedArgs a;
+        memset(&a, 0, sizeof(a));
+        auto k1 = [&](int r) { return (const cpx<float>*)ih.k1[ih.r1[r]]; };
+        for (int c = 0; c < 3; ++c) {
+            const int r = 12 * c;
+            // each D2 field reads the spectrum of its plain field
+            for (int q : {0, 4, 8})
+                if (ih.r1[r + q + 3] != ih.r1[r + q] || !ih.d2[r + q + 3] || ih.d2[r + q]) {
+                    fail(LDDMM_ERR_DEVICE_CHECK);
+                    return;
+                }
+            a.in[6 * c + 0] = k1(r);
+            a.in[6 * c + 1] = k1(r + 1);
+            a.in[6 * c + 2] = k1(r + 2);
+            a.in[6 * c + 3] = k1(r + 4);
+            a.in[6 * c + 4] = k1(r + 5);
+            a.in[6 * c + 5] = k1(r + 6);
+            a.in[18 + 3 * c] = k1(r + 8);
+            a.in[19 + 3 * c] = k1(r + 9);
+            a.in[20 + 3 * c] = k1(r + 10);
+        }
+        std::vector<G> g2;
+        for (int o = 0; o < 6; ++o) {
+            const SymD& sy = outs[o].terms[0].sym;
+            g2.push_back({o, sy.lpow, sy.scale, 2, 1, palloc(), 1});
+            a.out[o] = (cpx<float>*)g2.back().buf;
+        }
+        fused_launch(a, sidx, 0);
+        forward_tail(outs, g2, true);
+    }
+    // adjoint stage: requests (K ybar_eta_c, P ybar_xi_c) for c = 0..2;
+    // outputs per c: groups (s, f) of R'^T without L and under -L into eta_c,
+    // of ad_v^T into xi_c, each as (cls 2, cls 0, cls 1) partial spectra
+    void adjoint_stage_fused(const std::vector<SpecLin>& srcs, const std::vector<InvReq>& reqs,
+                             const std::vector<FwdOut>& outs, int sidx, const T* eta) {
+        const InvHead ih = inverse_head(srcs, reqs, true);
+        FusedArgs a;
+        memset(&a, 0, sizeof(a));
+        for (int c = 0; c < 3; ++c) {
+            if (ih.d2[2 * c] || ih.d2[2 * c + 1]) {
+                fail(LDDMM_ERR_DEVICE_CHECK);
+                return;
+            }
+            a.in[c] = (const cpx<float>*)ih.k1[ih.r1[2 * c]];
+            a.in[3 + c] = (const cpx<float>*)ih.k1[ih.r1[2 * c + 1]];
+        }
+        std::vector<G> g2;
+        for (int c = 0; c < 3; ++c)
+            for (int g = 0; g < 3; ++g)
+                for (int cls : {2, 0, 1}) {
+                    g2.push_back({g < 2 ? c : 3 + c, g == 1 ? 1 : 0, g == 1 ? -1.0 : 1.0, cls, 1, palloc(), 1});
+                    a.out[g2.size() - 1] = (cpx<float>*)g2.back().buf;
+                }
+        a.eta_src = (const float*)eta;
+        fused_launch(a, sidx, 1);
+        forward_tail(outs, g2, true);
     }
 
     // adjoint: from adj[0] = (ybar_eta, ybar_xi) at t = 1; result in adj[nt % 2].
@@ -1380,15 +1537,6 @@ class Engine : public EngineBase {
                     reqs.push_back({c, sym(1.0, -1, -1, 1), Y + c * d.N});
                     reqs.push_back({3 + c, sym(1.0, 0, -1, 1), Y + (3 + c) * d.N});
                 }
-                inverse(srcs, reqs, true);
-                {
-                    PScope ps_(this, KC_ADJPW, 24.0 * d.N * state_elem() + 42.0 * d.N * sizeof(T));
-                    if (bf16)
-                        k_adjoint_pw<T, __nv_bfloat16><<<pw_grid(d.N), PW_THREADS, 0, st>>>(
-                            StatePtr<__nv_bfloat16>{state_bf(sidx), d.N}, Y, G, d.N);
-                    else
-                        k_adjoint_pw<T, T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{state(sidx), d.N}, Y, G, d.N);
-                }
                 std::vector<FwdOut> outs(6);
                 for (int c = 0; c < 3; ++c) {
                     FwdOut& oe = outs[c];
@@ -1419,6 +1567,20 @@ class Engine : public EngineBase {
                         ox.bases.push_back({cx + c * d.NS, 1.0});
                         ox.bases.push_back({axp + c * d.NS, 0.5 * dt_});
                     }
+                }
+                if (fused) {
+                    adjoint_stage_fused(srcs, reqs, outs, sidx,
+                                        stg == 1 && eta_src ? eta_src + (size_t)3 * k * d.N : nullptr);
+                    continue;
+                }
+                inverse(srcs, reqs, true);
+                {
+                    PScope ps_(this, KC_ADJPW, 24.0 * d.N * state_elem() + 42.0 * d.N * sizeof(T));
+                    if (bf16)
+                        k_adjoint_pw<T, __nv_bfloat16><<<pw_grid(d.N), PW_THREADS, 0, st>>>(
+                            StatePtr<__nv_bfloat16>{state_bf(sidx), d.N}, Y, G, d.N);
+                    else
+                        k_adjoint_pw<T, T><<<pw_grid(d.N), PW_THREADS, 0, st>>>(StatePtr<T>{state(sidx), d.N}, Y, G, d.N);
                 }
                 forward(outs, true);
             }

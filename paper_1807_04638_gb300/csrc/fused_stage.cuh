@@ -1,0 +1,452 @@
+// Fused Jacobi stages (FP32 form, band-limited transforms).
+//
+// One stage of the tangent sweep (Sec. 3, incremental EPDiff and Jacobi
+// field) is: an inverse transform of (eta, xi) into 36 real fields, the
+// pointwise products p = ad*_eta m + ad*_v mu, q = ad_v xi with the stored
+// state, and a forward transform of (p, q).  One stage of the adjoint sweep
+// (its exact transpose) is: an inverse transform into the 6 fields
+// (K ybar_eta, P ybar_xi), the 36 pointwise group fields of the transposed
+// products, and their forward transforms.  The axis-0 and axis-1 passes stay
+// as they are; these kernels replace, for a tile of grid rows, the axis-2
+// pass of the inverse transform, the pointwise kernel and the axis-2 pass of
+// the forward transform, so that the real fields of a stage never leave the
+// SM: each grid row is held by one line group of threads from its first
+// inverse line transform to its last forward one.
+//
+// Geometry (register-blocked plans with E = 8 elements per thread):
+//   a block of FAST_THREADS threads is TL line groups of TPL = N / 8 threads;
+//   a tile is TL consecutive grid rows, one per line group; thread t of a
+//   group owns the points t + TPL*m (m < 8) of its row for the whole tile.
+//   A complex line transform packs two real fields of the same row.
+//   Inputs and outputs are band planes k2 < nb2 in the [k2][row] layout of
+//   the axis-2 pass; the next line's inputs are copied (cp.async) into the
+//   other half of a double buffer while the current line is transformed.
+//
+// Tangent (KIND 0): inputs in[27], axis-1 outputs of the inverse transform,
+//   for c = 0..2:  in[6c + 0] eta_c (gives eta_c and D2 eta_c),
+//                  in[6c + 1], in[6c + 2] D0 eta_c, D1 eta_c,
+//                  in[6c + 3] mu_c = (L eta)_c (gives mu_c and D2 mu_c),
+//                  in[6c + 4], in[6c + 5] D0 mu_c, D1 mu_c,
+//                  in[18 + 3c] xi_c (gives xi_c and D2 xi_c),
+//                  in[19 + 3c], in[20 + 3c] D0 xi_c, D1 xi_c;
+//   18 inverse line transforms per row accumulate p and q in registers;
+//   outputs out[0..5] = F2(p_0..2), F2(q_0..2), the plain axis-2 transforms.
+// Adjoint (KIND 1): inputs in[0..2] = K ybar_eta (y), in[3..5] = P ybar_xi
+//   (yx); y and yx are kept in registers; the
+//   9 groups (s, f_0, f_1, f_2) of the transposed products give 27 outputs,
+//   for c = 0..2 and group g = 0 (R'^T without L), 1 (R'^T under -L),
+//   2 (ad_v^T):  out[9c + 3g] = F2(s) + i kappa_2 F2(f_2),
+//                out[9c + 3g + 1] = F2(f_0), out[9c + 3g + 2] = F2(f_1);
+//   optional real cotangents eta_src (3 fields) are added to s of group 0.
+//   Its line transforms pack two rows of one field, as the separate axis-2
+//   pass does (fields of one row can differ widely in size, and a transform
+//   that packed two of them would leave the rounding of the larger in the
+//   smaller, which the derivative symbols then amplify): each field is handed
+//   between the row's owner and the row pair's line group through shared
+//   memory.
+#pragma once
+#include "fft_fast.cuh"
+#include "pw_kernels.cuh"
+
+namespace lddmm {
+
+constexpr int FUSED_NIN = 27, FUSED_NOUT = 27;
+constexpr int FUSED_BLOCKS = 2;  // resident blocks per SM
+
+struct FusedArgs {
+    const cpx<float>* in[FUSED_NIN];
+    cpx<float>* out[FUSED_NOUT];
+    const void* states;     // 24 state fields (float or bfloat16), stride npts
+    const float* eta_src;   // adjoint: 3 real fields added to s of group 0, or null
+    const float* dk2;       // kappa_2 with the Nyquist entry zeroed (n2/2 + 1)
+    const cpx<float>* tw;   // axis-2 twiddles
+    int rows, nb2, ntiles;
+    unsigned npts;          // points per field
+};
+
+template <int N> struct FusedGeom {
+    static_assert(FastPlan<N>::E == 8, "fused stages use the E = 8 plans");
+    static constexpr int E = 8;
+    static constexpr int TPL = N / E;
+    static constexpr int TL = FAST_THREADS / TPL;  // rows per tile
+    static constexpr int NH = N / 2 + 1;
+    static constexpr int SP = TL + 2;              // staged plane pitch (complex; 16-byte rows)
+    static constexpr int STG = 2 * NH * SP;        // one stage buffer: two inputs
+    static constexpr int XT = TL * SIdx<float, N, 1>::LP;  // one exchange tile
+    static constexpr int PH = (NH % 2 == 0) ? NH + 1 : NH;  // H pitch
+    static constexpr int HS = 2 * TL * PH;         // two unpacked outputs
+    static constexpr int CPK = TL * 8 / 16;        // 16-byte chunks per staged plane
+    static constexpr int RP = N + 8;               // adjoint hand-off row pitch (floats)
+    static constexpr size_t SMEM0 = (size_t)(2 * STG + 2 * XT + HS) * sizeof(cpx<float>);
+    static constexpr size_t SMEM1 = SMEM0 + (size_t)2 * TL * RP * sizeof(float);
+    static_assert(TL % 2 == 0, "the adjoint pairs the rows of a tile");
+};
+
+__device__ __forceinline__ float ldst(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldst(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+
+// Stored-state field f of this thread's point m (state layout of pw_kernels.cuh)
+template <class SS> struct PtState {
+    const SS* p;  // this thread's first point of field 0
+    unsigned n;   // field stride
+    __device__ __forceinline__ float operator()(int f, int m, int tpl) const { return ldst(p + f * n + tpl * m); }
+};
+// field indices
+__device__ __forceinline__ constexpr int fV(int c) { return c; }
+__device__ __forceinline__ constexpr int fDv(int c, int j) { return 3 + 3 * c + j; }  // D_j v_c
+__device__ __forceinline__ constexpr int fM(int c) { return 12 + c; }
+__device__ __forceinline__ constexpr int fDm(int c, int j) { return 15 + 3 * c + j; }  // D_j m_c
+
+// Tangent: contributions of inverse line L (c = L / 6, type L % 6) to
+// acc = (p_0, p_1, p_2, q_0, q_1, q_2):
+//   p_i = m_i div eta + mu_i div v + sum_j (D_i eta_j m_j + D_j m_i eta_j + D_i v_j mu_j + D_j mu_i v_j)
+//   q_i = sum_j (D_j v_i xi_j - D_j xi_i v_j)
+template <int L, int E, int TPL, class SS>
+__device__ __forceinline__ void tan_contrib(float (&acc)[6][E], const cpx<float> (&x)[E], const PtState<SS>& S) {
+    constexpr int C = L / 6, TY = L % 6;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const float a = x[m].x, b = x[m].y;
+        if constexpr (TY == 0) {  // (eta_C, D_2 eta_C)
+            acc[0][m] += S(fDm(0, C), m, TPL) * a;
+            acc[1][m] += S(fDm(1, C), m, TPL) * a;
+            acc[2][m] += S(fDm(2, C), m, TPL) * a;
+            const float mC = S(fM(C), m, TPL);
+            acc[2][m] += b * mC;
+            if constexpr (C == 2) {
+                acc[0][m] += S(fM(0), m, TPL) * b;
+                acc[1][m] += S(fM(1), m, TPL) * b;
+                acc[2][m] += mC * b;
+            }
+        } else if constexpr (TY == 1) {  // (D_0 eta_C, D_1 eta_C)
+            const float mC = S(fM(C), m, TPL);
+            acc[0][m] += a * mC;
+            acc[1][m] += b * mC;
+            if constexpr (C < 2) {
+                const float dd = C == 0 ? a : b;  // D_C eta_C, a term of div eta
+#pragma unroll
+                for (int k = 0; k < 3; ++k) acc[k][m] += (k == C ? mC : S(fM(k), m, TPL)) * dd;
+            }
+        } else if constexpr (TY == 2) {  // (mu_C, D_2 mu_C)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) acc[i][m] += S(fDv(C, i), m, TPL) * a;
+            const float divv = S(fDv(0, 0), m, TPL) + S(fDv(1, 1), m, TPL) + S(fDv(2, 2), m, TPL);
+            acc[C][m] += a * divv;
+            acc[C][m] += b * S(fV(2), m, TPL);
+        } else if constexpr (TY == 3) {  // (D_0 mu_C, D_1 mu_C)
+            acc[C][m] += a * S(fV(0), m, TPL);
+            acc[C][m] += b * S(fV(1), m, TPL);
+        } else if constexpr (TY == 4) {  // (xi_C, D_2 xi_C)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) acc[3 + i][m] += S(fDv(i, C), m, TPL) * a;
+            acc[3 + C][m] -= b * S(fV(2), m, TPL);
+        } else {  // (D_0 xi_C, D_1 xi_C)
+            acc[3 + C][m] -= a * S(fV(0), m, TPL);
+            acc[3 + C][m] -= b * S(fV(1), m, TPL);
+        }
+    }
+}
+
+// Adjoint: the two real fields of forward line F (c = F / 6, type F % 6) from
+// y = K ybar_eta = acc[0..2], yx = P ybar_xi = acc[3..5] and the state:
+//   group 0:  s = -sum_i D_c m_i y_i,          f_j = m_c y_j + delta_jc (m . y)
+//   group 1:  s = sum_i D_i v_c y_i + (div v) y_c,  f_j = -v_j y_c
+//   group 2:  s = sum_i D_c v_i yx_i,          f_j = v_j yx_c
+// even types pack (s, f_2), odd types (f_0, f_1).
+template <int F, int E, int TPL, class SS>
+__device__ __forceinline__ void adj_fields(cpx<float> (&x)[E], const float (&acc)[6][E], const PtState<SS>& S,
+                                           const float* eta, unsigned npts) {
+    constexpr int C = F / 6, TY = F % 6;
+    const float(&y)[6][E] = acc;  // y_i = acc[i], yx_i = acc[3 + i]
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        float a, b;
+        if constexpr (TY == 0 || TY == 1) {
+            const float mC = S(fM(C), m, TPL);
+            float my = 0.f;
+            if constexpr ((TY == 0 && C == 2) || (TY == 1 && C < 2))
+                my = S(fM(0), m, TPL) * y[0][m] + S(fM(1), m, TPL) * y[1][m] + S(fM(2), m, TPL) * y[2][m];
+            if constexpr (TY == 0) {
+                a = 0.f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) a -= S(fDm(i, C), m, TPL) * y[i][m];
+                if (eta) a += __ldg(eta + C * npts + TPL * m);
+                b = mC * y[2][m] + (C == 2 ? my : 0.f);
+            } else {
+                a = mC * y[0][m] + (C == 0 ? my : 0.f);
+                b = mC * y[1][m] + (C == 1 ? my : 0.f);
+            }
+        } else if constexpr (TY == 2 || TY == 3) {
+            if constexpr (TY == 2) {
+                const float divv = S(fDv(0, 0), m, TPL) + S(fDv(1, 1), m, TPL) + S(fDv(2, 2), m, TPL);
+                a = divv * y[C][m];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) a += S(fDv(C, i), m, TPL) * y[i][m];
+                b = -S(fV(2), m, TPL) * y[C][m];
+            } else {
+                a = -S(fV(0), m, TPL) * y[C][m];
+                b = -S(fV(1), m, TPL) * y[C][m];
+            }
+        } else {
+            if constexpr (TY == 4) {
+                a = 0.f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) a += S(fDv(i, C), m, TPL) * y[3 + i][m];
+                b = S(fV(2), m, TPL) * y[3 + C][m];
+            } else {
+                a = S(fV(0), m, TPL) * y[3 + C][m];
+                b = S(fV(1), m, TPL) * y[3 + C][m];
+            }
+        }
+        x[m] = mk(a, b);
+    }
+}
+
+// inputs of inverse line l: (i0, i1); i1 = -1: the line packs (in[i0],
+// D2 in[i0]) (tangent only)
+template <int KIND> __device__ __forceinline__ void fused_line_inputs(int l, int& i0, int& i1) {
+    if constexpr (KIND == 0) {
+        const int c = l / 6, ty = l - 6 * c;
+        if (ty < 4) {
+            i0 = 6 * c + (ty < 2 ? 0 : 3) + (ty & 1);
+            i1 = (ty & 1) ? i0 + 1 : -1;
+        } else {
+            i0 = 18 + 3 * c + (ty - 4);
+            i1 = ty == 5 ? i0 + 1 : -1;
+        }
+    } else {
+        // (y0, y1), (y2, yx0), (yx1, yx2)
+        i0 = 2 * l;
+        i1 = 2 * l + 1;
+    }
+}
+
+template <class SS, int N, int KIND>
+__global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(const __grid_constant__ FusedArgs a) {
+    using G = FusedGeom<N>;
+    constexpr int E = G::E, TPL = G::TPL, TL = G::TL, NH = G::NH, SP = G::SP, PH = G::PH, RP = G::RP;
+    constexpr int NLI = KIND == 0 ? 18 : 3;   // inverse lines per row (tangent) / rounds (adjoint)
+    constexpr int NLO = KIND == 0 ? 3 : 18;   // forward lines per row / rounds
+    constexpr int HALF = TL / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<float>* const stage0 = (cpx<float>*)smem_raw;  // buffers stage0 + sb * STG
+    cpx<float>* const b0 = stage0 + 2 * G::STG;
+    cpx<float>* const b1 = b0 + G::XT;
+    cpx<float>* const H = b1 + G::XT;
+    float* const R = (float*)(H + G::HS);  // adjoint: two real fields of the tile's rows, pitch RP
+    const int c = threadIdx.x / TPL, t = threadIdx.x % TPL;
+    // adjoint: a line group transforms one field (q) on a pair of rows (2 rp, 2 rp + 1)
+    const int q = c >= HALF, rp = c - q * HALF;
+    const int rows = a.rows, nb2 = a.nb2, ntiles = a.ntiles;
+
+    auto issue = [&](int tile, int l, int buf) {
+        if (tile < ntiles) {
+            int i0, i1;
+            fused_line_inputs<KIND>(l, i0, i1);
+            const int nin = i1 >= 0 ? 2 : 1;  // staged inputs
+            const int per = nb2 * G::CPK;
+            cpx<float>* dst = stage0 + buf * G::STG;
+            const size_t r0 = (size_t)tile * TL;
+            for (int i = threadIdx.x; i < nin * per; i += FAST_THREADS) {
+                const int qq = i >= per;
+                const int rem = i - qq * per;
+                const int k = rem / G::CPK, ch = rem % G::CPK;
+                const cpx<float>* src = a.in[qq ? i1 : i0] + (size_t)k * rows + r0;
+                cp_async16(dst + qq * NH * SP + k * SP + 2 * ch, src + 2 * ch);
+            }
+        }
+        cp_async_commit();
+    };
+
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    issue(tile, 0, 0);
+    int sb = 0;
+    const SS* const states = (const SS*)a.states;
+    cpx<float> x[E];
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * TL;
+        const PtState<SS> S{states + (size_t)(r0 + c) * N + t, a.npts};
+        // tangent: p, q accumulators; adjoint: y, yx
+        float acc[6][E];
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+#pragma unroll
+            for (int m = 0; m < E; ++m) acc[f][m] = 0.f;
+        // ---------------- inverse lines
+        for (int l = 0; l < NLI; ++l) {
+            const int nl = l + 1 < NLI ? l + 1 : 0;
+            issue(l + 1 < NLI ? tile : tile + gridDim.x, nl, sb ^ 1);
+            cp_async_wait<1>();
+            __syncthreads();
+            const cpx<float>* const stg = stage0 + sb * G::STG;
+            if constexpr (KIND == 0) {
+                // two fields of this line group's row: (in[i0], D2 in[i0]) or (in[i0], in[i1])
+                int i0, i1;
+                fused_line_inputs<KIND>(l, i0, i1);
+                const cpx<float>* SA = stg + c;
+                const cpx<float>* SB = SA + NH * SP;
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int k = t + TPL * m;
+                    const bool lo = k < NH;
+                    const int kk = lo ? k : N - k;
+                    cpx<float> u = mk(0.f, 0.f), v = mk(0.f, 0.f);
+                    if (kk < nb2) {
+                        u = SA[kk * SP];
+                        if (i1 < 0) {
+                            const float d = __ldg(a.dk2 + kk);
+                            v = mk(-d * u.y, d * u.x);
+                        } else {
+                            v = SB[kk * SP];
+                        }
+                    }
+                    if (kk == 0 || kk == N / 2) {
+                        u.y = 0.f;
+                        v.y = 0.f;
+                    }
+                    if (!lo) {
+                        u = cj(u);
+                        v = cj(v);
+                    }
+                    x[m] = mk(u.x - v.y, u.y + v.x);
+                }
+            } else {
+                // one field (input q of the line) on a pair of rows
+                const cpx<float>* SA = stg + q * NH * SP + 2 * rp;
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int k = t + TPL * m;
+                    const bool lo = k < NH;
+                    const int kk = lo ? k : N - k;
+                    cpx<float> u = mk(0.f, 0.f), v = mk(0.f, 0.f);
+                    if (kk < nb2) {
+                        u = SA[kk * SP];
+                        v = SA[kk * SP + 1];
+                    }
+                    if (kk == 0 || kk == N / 2) {
+                        u.y = 0.f;
+                        v.y = 0.f;
+                    }
+                    if (!lo) {
+                        u = cj(u);
+                        v = cj(v);
+                    }
+                    x[m] = mk(u.x - v.y, u.y + v.x);
+                }
+            }
+            fast_fft<float, N, 1>(x, b0, b1, c, t, a.tw, +1);
+            if constexpr (KIND == 0) {
+                switch (l) {
+#define LDDMM_TC(L) \
+    case L: tan_contrib<L, E, TPL>(acc, x, S); break;
+                    LDDMM_TC(0) LDDMM_TC(1) LDDMM_TC(2) LDDMM_TC(3) LDDMM_TC(4) LDDMM_TC(5)
+                    LDDMM_TC(6) LDDMM_TC(7) LDDMM_TC(8) LDDMM_TC(9) LDDMM_TC(10) LDDMM_TC(11)
+                    LDDMM_TC(12) LDDMM_TC(13) LDDMM_TC(14) LDDMM_TC(15) LDDMM_TC(16) LDDMM_TC(17)
+#undef LDDMM_TC
+                    default: break;
+                }
+            } else {
+                // hand the row pair to the rows' owners: acc[2l], acc[2l + 1]
+                float* const Rq = R + (q * TL + 2 * rp) * RP + t;
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    Rq[TPL * m] = x[m].x;
+                    Rq[RP + TPL * m] = x[m].y;
+                }
+                __syncthreads();
+                const float* const Ro = R + c * RP + t;
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const float f0 = Ro[TPL * m], f1 = Ro[TL * RP + TPL * m];
+                    if (l == 0) {
+                        acc[0][m] = f0;
+                        acc[1][m] = f1;
+                    } else if (l == 1) {
+                        acc[2][m] = f0;
+                        acc[3][m] = f1;
+                    } else {
+                        acc[4][m] = f0;
+                        acc[5][m] = f1;
+                    }
+                }
+            }
+            sb ^= 1;
+        }
+        // ---------------- forward lines
+        for (int f = 0; f < NLO; ++f) {
+            if constexpr (KIND == 0) {
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    if (f == 0) x[m] = mk(acc[0][m], acc[1][m]);
+                    else if (f == 1) x[m] = mk(acc[2][m], acc[3][m]);
+                    else x[m] = mk(acc[4][m], acc[5][m]);
+                }
+            } else {
+                const float* eta = a.eta_src ? a.eta_src + (size_t)(r0 + c) * N + t : nullptr;
+                switch (f) {
+#define LDDMM_AF(F) \
+    case F: adj_fields<F, E, TPL>(x, acc, S, eta, a.npts); break;
+                    LDDMM_AF(0) LDDMM_AF(1) LDDMM_AF(2) LDDMM_AF(3) LDDMM_AF(4) LDDMM_AF(5)
+                    LDDMM_AF(6) LDDMM_AF(7) LDDMM_AF(8) LDDMM_AF(9) LDDMM_AF(10) LDDMM_AF(11)
+                    LDDMM_AF(12) LDDMM_AF(13) LDDMM_AF(14) LDDMM_AF(15) LDDMM_AF(16) LDDMM_AF(17)
+#undef LDDMM_AF
+                    default: break;
+                }
+                // the two fields of this row go to the line groups that
+                // transform them on row pairs (two rows of one field share a
+                // transform, as in the separate axis-2 pass)
+                float* const Ro = R + c * RP + t;
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    Ro[TPL * m] = x[m].x;
+                    Ro[TL * RP + TPL * m] = x[m].y;
+                }
+                __syncthreads();
+                const float* const Rq = R + (q * TL + 2 * rp) * RP + t;
+#pragma unroll
+                for (int m = 0; m < E; ++m) x[m] = mk(Rq[TPL * m], Rq[RP + TPL * m]);
+            }
+            fast_fft<float, N, 1>(x, b0, b1, c, t, a.tw, -1);
+            // stage the packed spectrum to pair Z_k with Z_{N-k}
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; ++m) b0[SIdx<float, N, 1>::at(c, t + TPL * m)] = x[m];
+            __syncthreads();
+            // tangent: H[0][row] and H[1][row] are the two fields of the row;
+            // adjoint: H[q][row] is field q of the line
+            const int ha = KIND == 0 ? c : q * TL + 2 * rp;
+            const int hb = KIND == 0 ? TL + c : q * TL + 2 * rp + 1;
+            for (int k = t; k < nb2; k += TPL) {
+                const cpx<float> zk = b0[SIdx<float, N, 1>::at(c, k)];
+                const cpx<float> zn = cj(b0[SIdx<float, N, 1>::at(c, k == 0 ? 0 : N - k)]);
+                H[ha * PH + k] = 0.5f * (zk + zn);
+                H[hb * PH + k] = rot(0.5f * (zk - zn), -1);
+            }
+            __syncthreads();
+            // outputs of this line: one combined F(s) + i kappa_2 F(f_2), or two plain
+            const bool combined = KIND == 1 && (f % 2 == 0);
+            int ob;
+            if constexpr (KIND == 0) ob = 2 * f;
+            else ob = 9 * (f / 6) + 3 * ((f % 6) / 2) + (combined ? 0 : 1);
+            if (combined) {
+                for (int i = threadIdx.x; i < nb2 * TL; i += FAST_THREADS) {
+                    const int k = i / TL, row = i % TL;
+                    const float d = __ldg(a.dk2 + k);
+                    const cpx<float> fs = H[row * PH + k], f2 = H[(TL + row) * PH + k];
+                    a.out[ob][(size_t)k * rows + r0 + row] = fs + mk(-d * f2.y, d * f2.x);
+                }
+            } else {
+                for (int i = threadIdx.x; i < 2 * nb2 * TL; i += FAST_THREADS) {
+                    const int qq = i / (nb2 * TL);
+                    const int rem = i - qq * nb2 * TL;
+                    const int k = rem / TL, row = rem % TL;
+                    a.out[ob + qq][(size_t)k * rows + r0 + row] = H[(qq * TL + row) * PH + k];
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace lddmm

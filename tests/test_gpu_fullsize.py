@@ -186,12 +186,15 @@ def test_metric_160_192_96(pkg, prec):
 def test_band_limited_passes_equal_full_transforms(pkg, workload128, monkeypatch):
     """With the 2/3-rule projector the shooting and Jacobi-sweep transforms
     touch only the band; the results equal those of full transforms (the
-    skipped entries are zero or only ever used through P)."""
+    skipped entries are zero or only ever used through P).  Both runs use
+    the separate axis-2 passes (the full transforms have no fused stage);
+    the fused stages are compared with them in test_gpu_fused.py."""
     P, v0t, e0, e1, d = workload128
     n = (128, 128, 128)
     f32 = torch.float32
     prm = pkg.default_params(alpha=0.005, nt=10, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32)
     out = {}
+    monkeypatch.setenv("LDDMM_UNFUSED", "1")
     for mode in ("band", "full"):
         if mode == "full":
             monkeypatch.setenv("LDDMM_FULL_BAND", "1")
