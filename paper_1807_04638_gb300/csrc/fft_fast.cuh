@@ -116,7 +116,9 @@ template <class T, int N, int MAP> struct SIdx {
     }
 };
 
-template <class T, int N, int E, int TPL, int RADS, int S, int NS, int MAP>
+// TWS: the twiddle table tw is in shared memory (else global, read through
+// the read-only cache)
+template <class T, int N, int E, int TPL, int RADS, int S, int NS, int MAP, bool TWS = false>
 __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* b1, int c, int t, const cpx<T>* tw,
                                             int dir) {
     constexpr int R = (RADS >> (4 * S)) & 0xF;
@@ -132,7 +134,7 @@ __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* 
         for (int r = 0; r < R; ++r) {
             cpx<T> a = x[b + B * r];
             if (NS > 1 && r > 0) {
-                cpx<T> w = ldg(&tw[k * r * (N / (NS * R))]);
+                cpx<T> w = TWS ? tw[k * r * (N / (NS * R))] : ldg(&tw[k * r * (N / (NS * R))]);
                 if (dir > 0) w.y = -w.y;
                 a = a * w;
             }
@@ -152,16 +154,16 @@ __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* 
         __syncthreads();
 #pragma unroll
         for (int m = 0; m < E; ++m) x[m] = b0[SIdx<T, N, MAP>::at(c, t + TPL * m)];
-        fast_stages<T, N, E, TPL, RADS, S + 1, NS * R, MAP>(x, b1, b0, c, t, tw, dir);
+        fast_stages<T, N, E, TPL, RADS, S + 1, NS * R, MAP, TWS>(x, b1, b0, c, t, tw, dir);
     }
 }
 
-template <class T, int N, int MAP>
+template <class T, int N, int MAP, bool TWS = false>
 __device__ __forceinline__ void fast_fft(cpx<T> (&x)[FastPlan<N>::E], cpx<T>* b0, cpx<T>* b1, int c, int t,
                                          const cpx<T>* tw, int dir) {
     constexpr int E = FastPlan<N>::E;
     __syncthreads();  // the tiles may still be read by the previous transform
-    fast_stages<T, N, E, N / E, FastPlan<N>::RADS, 0, 1, MAP>(x, b0, b1, c, t, tw, dir);
+    fast_stages<T, N, E, N / E, FastPlan<N>::RADS, 0, 1, MAP, TWS>(x, b0, b1, c, t, tw, dir);
 }
 
 // ---------------------------------------------------------------- async copies

@@ -76,9 +76,14 @@ template <int N> struct FusedGeom {
     static constexpr int PH = (NH % 2 == 0) ? NH + 1 : NH;  // H pitch
     static constexpr int HS = 2 * TL * PH;         // two unpacked outputs
     static constexpr int CPK = TL * 8 / 16;        // 16-byte chunks per staged plane
-    static constexpr int RP = N + 8;               // adjoint hand-off row pitch (floats)
-    static constexpr size_t SMEM0 = (size_t)(2 * STG + 2 * XT + HS) * sizeof(cpx<float>);
-    static constexpr size_t SMEM1 = SMEM0 + (size_t)2 * TL * RP * sizeof(float);
+    // adjoint hand-off of two real fields: row pitch RP and field stride FS
+    // (floats), both 16 banks apart modulo 32, so that neither the two rows
+    // nor the two fields a warp touches share a bank
+    static constexpr int RP = N + 16;
+    static constexpr int FS = TL * RP + 16;
+    static constexpr int TWD = N + (NH + 1) / 2;   // twiddles, then kappa_2 (complex slots)
+    static constexpr size_t SMEM0 = (size_t)(2 * STG + 2 * XT + HS + TWD) * sizeof(cpx<float>);
+    static constexpr size_t SMEM1 = SMEM0 + (size_t)2 * FS * sizeof(float);
     static_assert(TL % 2 == 0, "the adjoint pairs the rows of a tile");
 };
 
@@ -96,6 +101,49 @@ __device__ __forceinline__ constexpr int fV(int c) { return c; }
 __device__ __forceinline__ constexpr int fDv(int c, int j) { return 3 + 3 * c + j; }  // D_j v_c
 __device__ __forceinline__ constexpr int fM(int c) { return 12 + c; }
 __device__ __forceinline__ constexpr int fDm(int c, int j) { return 15 + 3 * c + j; }  // D_j m_c
+
+// The q-th state field that line (c, type) reads (-1 past the last), the
+// same for the tangent's inverse lines and the adjoint's forward lines (see
+// tan_contrib and adj_fields); at most 6.
+__device__ __forceinline__ int line_field(int c, int ty, int q) {
+    switch (ty) {
+        case 0:  // D_c m_0..2, m_c (and m_0, m_1 for c = 2)
+            if (q < 3) return fDm(q, c);
+            if (q == 3) return fM(c);
+            return c == 2 && q < 6 ? fM(q - 4) : -1;
+        case 1:  // m_c (and every m_k for c < 2)
+            if (c == 2) return q == 0 ? fM(2) : -1;
+            return q < 3 ? fM(q) : -1;
+        case 2:  // D_0..2 v_c, the other two diagonal entries of D v, v_2
+            if (q < 3) return fDv(c, q);
+            if (q < 5) {
+                const int i = q - 3 + (q - 3 >= c ? 1 : 0);
+                return fDv(i, i);
+            }
+            return q == 5 ? fV(2) : -1;
+        case 4:  // D_c v_0..2, v_2
+            if (q < 3) return fDv(q, c);
+            return q == 3 ? fV(2) : -1;
+        default:  // v_0, v_1
+            return q < 2 ? fV(q) : -1;
+    }
+}
+
+// Bring the state rows of a tile that line (c, type) reads into L1 (one
+// prefetch per 128-byte line), ahead of the loads of its products, so that
+// those loads do not wait on L2.
+template <class SS, int N, int TL>
+__device__ __forceinline__ void prefetch_line_fields(const SS* tile_states, unsigned npts, int c, int ty) {
+    // the tile's rows of one field are contiguous: PER cache lines
+    constexpr int PER = (int)(TL * N * sizeof(SS) / 128);
+    static_assert(PER * 128 == TL * N * sizeof(SS), "whole cache lines per tile");
+    for (int i = threadIdx.x; i < 6 * PER; i += FAST_THREADS) {
+        const int f = line_field(c, ty, i / PER);
+        if (f < 0) break;
+        const char* p = (const char*)(tile_states + (size_t)f * npts) + (size_t)(i % PER) * 128;
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+    }
+}
 
 // Tangent: contributions of inverse line L (c = L / 6, type L % 6) to
 // acc = (p_0, p_1, p_2, q_0, q_1, q_2):
@@ -224,19 +272,20 @@ template <int KIND> __device__ __forceinline__ void fused_line_inputs(int l, int
 template <class SS, int N, int KIND>
 __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(const __grid_constant__ FusedArgs a) {
     using G = FusedGeom<N>;
-    constexpr int E = G::E, TPL = G::TPL, TL = G::TL, NH = G::NH, SP = G::SP, PH = G::PH, RP = G::RP;
+    constexpr int E = G::E, TPL = G::TPL, TL = G::TL, NH = G::NH, SP = G::SP, PH = G::PH, RP = G::RP, FS = G::FS;
     constexpr int NLI = KIND == 0 ? 18 : 3;   // inverse lines per row (tangent) / rounds (adjoint)
     constexpr int NLO = KIND == 0 ? 3 : 18;   // forward lines per row / rounds
-    constexpr int HALF = TL / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<float>* const stage0 = (cpx<float>*)smem_raw;  // buffers stage0 + sb * STG
     cpx<float>* const b0 = stage0 + 2 * G::STG;
     cpx<float>* const b1 = b0 + G::XT;
     cpx<float>* const H = b1 + G::XT;
-    float* const R = (float*)(H + G::HS);  // adjoint: two real fields of the tile's rows, pitch RP
+    cpx<float>* const tws = H + G::HS;                  // twiddles
+    float* const dks = (float*)(tws + N);              // kappa_2 (Nyquist zeroed)
+    float* const R = (float*)(tws + G::TWD);           // adjoint: two real fields of the tile's rows
     const int c = threadIdx.x / TPL, t = threadIdx.x % TPL;
     // adjoint: a line group transforms one field (q) on a pair of rows (2 rp, 2 rp + 1)
-    const int q = c >= HALF, rp = c - q * HALF;
+    const int q = c & 1, rp = c >> 1;
     const int rows = a.rows, nb2 = a.nb2, ntiles = a.ntiles;
 
     auto issue = [&](int tile, int l, int buf) {
@@ -260,12 +309,15 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
 
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
+    for (int i = threadIdx.x; i < N; i += FAST_THREADS) tws[i] = ldg(a.tw + i);
+    for (int i = threadIdx.x; i < NH; i += FAST_THREADS) dks[i] = __ldg(a.dk2 + i);
     issue(tile, 0, 0);
     int sb = 0;
     const SS* const states = (const SS*)a.states;
     cpx<float> x[E];
     for (; tile < ntiles; tile += gridDim.x) {
         const int r0 = tile * TL;
+        const SS* const tile_states = states + (size_t)r0 * N;
         const PtState<SS> S{states + (size_t)(r0 + c) * N + t, a.npts};
         // tangent: p, q accumulators; adjoint: y, yx
         float acc[6][E];
@@ -281,6 +333,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
             __syncthreads();
             const cpx<float>* const stg = stage0 + sb * G::STG;
             if constexpr (KIND == 0) {
+                prefetch_line_fields<SS, N, TL>(tile_states, a.npts, l / 6, l % 6);
                 // two fields of this line group's row: (in[i0], D2 in[i0]) or (in[i0], in[i1])
                 int i0, i1;
                 fused_line_inputs<KIND>(l, i0, i1);
@@ -295,7 +348,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                     if (kk < nb2) {
                         u = SA[kk * SP];
                         if (i1 < 0) {
-                            const float d = __ldg(a.dk2 + kk);
+                            const float d = dks[kk];
                             v = mk(-d * u.y, d * u.x);
                         } else {
                             v = SB[kk * SP];
@@ -312,6 +365,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                     x[m] = mk(u.x - v.y, u.y + v.x);
                 }
             } else {
+                if (l == NLI - 1) prefetch_line_fields<SS, N, TL>(tile_states, a.npts, 0, 0);
                 // one field (input q of the line) on a pair of rows
                 const cpx<float>* SA = stg + q * NH * SP + 2 * rp;
 #pragma unroll
@@ -335,7 +389,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                     x[m] = mk(u.x - v.y, u.y + v.x);
                 }
             }
-            fast_fft<float, N, 1>(x, b0, b1, c, t, a.tw, +1);
+            fast_fft<float, N, 1, true>(x, b0, b1, c, t, tws, +1);
             if constexpr (KIND == 0) {
                 switch (l) {
 #define LDDMM_TC(L) \
@@ -348,7 +402,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                 }
             } else {
                 // hand the row pair to the rows' owners: acc[2l], acc[2l + 1]
-                float* const Rq = R + (q * TL + 2 * rp) * RP + t;
+                float* const Rq = R + q * FS + 2 * rp * RP + t;
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
                     Rq[TPL * m] = x[m].x;
@@ -358,7 +412,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                 const float* const Ro = R + c * RP + t;
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
-                    const float f0 = Ro[TPL * m], f1 = Ro[TL * RP + TPL * m];
+                    const float f0 = Ro[TPL * m], f1 = Ro[FS + TPL * m];
                     if (l == 0) {
                         acc[0][m] = f0;
                         acc[1][m] = f1;
@@ -393,6 +447,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
 #undef LDDMM_AF
                     default: break;
                 }
+                if (f + 1 < NLO) prefetch_line_fields<SS, N, TL>(tile_states, a.npts, (f + 1) / 6, (f + 1) % 6);
                 // the two fields of this row go to the line groups that
                 // transform them on row pairs (two rows of one field share a
                 // transform, as in the separate axis-2 pass)
@@ -400,14 +455,14 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
                     Ro[TPL * m] = x[m].x;
-                    Ro[TL * RP + TPL * m] = x[m].y;
+                    Ro[FS + TPL * m] = x[m].y;
                 }
                 __syncthreads();
-                const float* const Rq = R + (q * TL + 2 * rp) * RP + t;
+                const float* const Rq = R + q * FS + 2 * rp * RP + t;
 #pragma unroll
                 for (int m = 0; m < E; ++m) x[m] = mk(Rq[TPL * m], Rq[RP + TPL * m]);
             }
-            fast_fft<float, N, 1>(x, b0, b1, c, t, a.tw, -1);
+            fast_fft<float, N, 1, true>(x, b0, b1, c, t, tws, -1);
             // stage the packed spectrum to pair Z_k with Z_{N-k}
             __syncthreads();
 #pragma unroll
@@ -432,7 +487,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
             if (combined) {
                 for (int i = threadIdx.x; i < nb2 * TL; i += FAST_THREADS) {
                     const int k = i / TL, row = i % TL;
-                    const float d = __ldg(a.dk2 + k);
+                    const float d = dks[k];
                     const cpx<float> fs = H[row * PH + k], f2 = H[(TL + row) * PH + k];
                     a.out[ob][(size_t)k * rows + r0 + row] = fs + mk(-d * f2.y, d * f2.x);
                 }
