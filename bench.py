@@ -54,12 +54,14 @@ def parse():
     ap.add_argument("--no-prof", action="store_true", help="skip the per-kernel profiled pass")
     ap.add_argument("--n", type=int, default=128, help="cubic grid size (profiling runs; the metric is 128)")
     ap.add_argument("--nt", type=int, default=NT, help="time steps (profiling runs; the metric uses 10)")
-    ap.add_argument("--serve-requests", type=int, default=8,
-                    help="requests of the serving trace (0: skip); the full serving workload is 256")
-    ap.add_argument("--plain-registration", action="store_true",
-                    help="also run the registration of the workload with the plain FP64 method")
-    ap.add_argument("--serve-fp64", type=int, default=0,
-                    help="also run the first M serving requests serially with the plain FP64 method")
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="requests of the serving trace, a prefix of its 256 (0: skip)")
+    ap.add_argument("--no-plain-registration", action="store_true",
+                    help="skip the registration of the workload with the plain FP64 method")
+    ap.add_argument("--serve-fp64", type=int, default=3,
+                    help="run the first M serving requests serially with the plain FP64 method (0: skip)")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the 256x300x256 registration (FP32, bfloat16 states, checkpointing)")
     return ap.parse_args()
 
 
@@ -260,6 +262,46 @@ def run_serving(args, dev):
     return out
 
 
+# ----------------------------------------------------------------------------- 256x300x256
+N3 = (256, 300, 256)
+
+
+def run_config3(dev, stream):
+    """Register the brain-shaped 256x300x256 volume (perturbed nested
+    ellipsoids with a 4-voxel boundary perturbation, noise 0.02; target =
+    the phantom shot by a |k| <= 8, 8-voxel velocity plus noise) in the FP32
+    form with bfloat16 stored states and forward states checkpointed every 2
+    steps: 10 Gauss-Newton iterations, PCG rtol 0.1, cap 50."""
+    import numpy as np
+    import torch
+
+    import paper_1807_04638_gb300 as pkg
+    from paper_1807_04638_gb300 import synth
+    P, v0t, e0, e1 = synth.ellipsoid_pair_inputs(N3, 2, kmax=8, max_disp_vox=8.0, noise_sigma=0.02,
+                                                 perturb_vox=4.0)
+    prm = pkg.default_params(alpha=ALPHA, nt=NT, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_BF16,
+                             checkpoint_every=2, gn_maxit=10, pcg_maxit=50, pcg_rtol=0.1)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    h = pkg.Handle(N3, prm, stream=stream, device=dev.index)
+    try:
+        m1 = h.new_img()
+        h.lddmm_shoot(T(v0t), T(P), m1)  # target (untimed)
+        I1 = (m1 + T(e1)).contiguous()
+        I0 = T(P + e0)
+        v = torch.zeros((3,) + N3, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = h.lddmm_register(I0, I1, v)
+        torch.cuda.synchronize(dev)
+        secs = time.perf_counter() - t0
+    finally:
+        h.close()
+    return {"grid": list(N3), "form": "FP32, bfloat16 stored states, checkpoint every 2 steps", "seconds": secs,
+            "workspace_gb": round(pkg.workspace_bytes(N3, prm) / 1e9, 2), "gn_iters": r["gn_iters"],
+            "pcg_iters_total": r["pcg_iters_total"], "mse_rel": r["mse_rel"], "gnorm_rel": r["gnorm_rel"],
+            "jac_min": r["jac_min"], "jac_max": r["jac_max"], "status": r["status"]}
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 def oracle_hv_sample(P, v0, d, stages=2):
     """Time the FP64 oracle on a bounded sample of one Hv at 128^3: `stages`
@@ -283,28 +325,63 @@ def cpu_cores_used():
     return 1  # numpy's pocketfft and the elementwise work run on one thread
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_hv_measured(P, v0, d, workers):
+    """One complete FP64 oracle Hv at 128^3 (tangent sweep, Gauss-Newton
+    source, adjoint sweep and assembly: O.hessvec), timed with its
+    transforms on `workers` threads (scipy.fft).  The linearisation point is
+    the EPDiff trajectory of v0 / 2, computed untimed without the map
+    transport, with the image at t = 1 taken as the phantom: the Hv's work
+    does not depend on those values."""
+    from oracle import lddmm_oracle as O
+    g = O.Grid(N128, alpha=ALPHA)
+    p = O.Params(alpha=ALPHA, nt=NT, weight=1e-3)
+    O.set_fft_workers(workers)
+    try:
+        tr = O.shoot(g, 0.5 * v0, NT, P, transport=False)
+        t0 = time.perf_counter()
+        O.hessvec(g, p, tr, d)
+        secs = time.perf_counter() - t0
+    finally:
+        O.set_fft_workers(None)
+    return 1.0 / secs, secs
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    from oracle import lddmm_oracle as O
     P, v0, e0, e1, d = workload_inputs()
-    for _ in range(args.warmup):
-        oracle_hv_sample(P, v0, d, stages=1)
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        v, _ = oracle_hv_sample(P, v0, d, stages=1)
-        vals.append(v)
-    wall = time.perf_counter() - t0
+    cores = host_cores()
+    O.set_fft_workers(cores)
+    try:
+        for _ in range(args.warmup):
+            oracle_hv_sample(P, v0, d, stages=1)
+        vals = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            v, _ = oracle_hv_sample(P, v0, d, stages=1)
+            vals.append(v)
+        wall = time.perf_counter() - t0
+    finally:
+        O.set_fft_workers(None)
     value = args.steps / sum(1.0 / v for v in vals)
     sample = ("per step: one forward Jacobi stage + one adjoint Jacobi stage of the FP64 NumPy oracle at 128^3 "
-              "(fixed linearisation state), scaled by 2*nt = 20 to one Hv")
+              f"(fixed linearisation state; transforms on {cores} threads through scipy.fft), scaled by "
+              "2*nt = 20 to one Hv")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": list(N128), "nt": NT},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -623,10 +700,25 @@ def finish(args, out, h, v0t, d, I0, I1, stream, dev, rank, P, NG):
                                           "pcg_iters_total": rl["pcg_iters_total"], "mse_rel": rl["mse_rel"],
                                           "gnorm_rel": rl["gnorm_rel"], "jac_min": rl["jac_min"],
                                           "jac_max": rl["jac_max"], "status": rl["status"]}
+        # the same registration at regularisation weight 1e-2, where the map
+        # stays diffeomorphic (min det J > 0) on this noisy workload
+        prmw = pkg.default_params(**{f: getattr(prm, f) for f, _ in prm._fields_})
+        prmw.weight = 1e-2
+        hw = pkg.Handle(NG, prmw, stream=stream, device=dev.index)
+        v = torch.zeros((3,) + NG, dtype=f32, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rw = hw.lddmm_register(I0, I1, v)
+        torch.cuda.synchronize(dev)
+        tw = time.perf_counter() - t0
+        hw.close()
+        out["registration_w1e-2"] = {"weight": 1e-2, "seconds": tw, "registrations_per_s": 1.0 / tw,
+                                     "gn_iters": rw["gn_iters"], "pcg_iters_total": rw["pcg_iters_total"],
+                                     "mse_rel": rw["mse_rel"], "gnorm_rel": rw["gnorm_rel"],
+                                     "jac_min": rw["jac_min"], "jac_max": rw["jac_max"], "status": rw["status"]}
 
-    # ---- the same registration with the plain FP64 method (opt-in: about
-    # ten times the FP32 form's time)
-    if args.plain_registration and rank == 0:
+    # ---- the same registration with the plain FP64 method
+    if not args.no_plain_registration and args.registrations > 0 and rank == 0:
         prm64 = pkg.default_params(**{f: getattr(prm, f) for f, _ in prm._fields_})
         prm64.compute_dtype, prm64.state_dtype = pkg.LDDMM_F64, pkg.LDDMM_F64
         h64 = pkg.Handle(NG, prm64, stream=stream, device=dev.index)
@@ -642,17 +734,29 @@ def finish(args, out, h, v0t, d, I0, I1, stream, dev, rank, P, NG):
                                           "gnorm_rel": r64["gnorm_rel"], "jac_min": r64["jac_min"],
                                           "jac_max": r64["jac_max"], "status": r64["status"]}
 
+    # ---- the 256x300x256 brain-shaped volume: FP32, bfloat16 states,
+    # checkpointed forward states, 10 Gauss-Newton iterations
+    if not args.no_config3 and args.registrations > 0 and rank == 0:
+        out["registration_256x300x256"] = run_config3(dev, stream)
+
     # ---- serving trace (continuous batching, mixed grid sizes)
     if args.serve_requests > 0 and rank == 0:
         out["serving"] = run_serving(args, dev)
 
-    # ---- CPU oracle on the host cores (bounded sample)
+    # ---- CPU oracle on the host cores: one complete Hv on every core, and a
+    # single-thread sample of Jacobi stages
     if not args.no_cpu and rank == 0 and tuple(NG) == N128:
+        cores = host_cores()
+        mv, msecs = oracle_hv_measured(P, v0t, d, cores)
         cv, secs = oracle_hv_sample(P, v0t, d, stages=2)
-        out["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+        out["cpu_baseline"] = {"value": mv, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "host_cores": os.cpu_count(),
-                               "sample": f"FP64 NumPy oracle: 2 forward + 2 adjoint Jacobi stages at 128^3 "
-                                         f"({secs:.1f} s), scaled by 2*nt/2 = 10 to one Hv"}
+                               "sample": f"one complete FP64 NumPy oracle Hv at 128^3, nt = 10 ({msecs:.1f} s), "
+                                         f"transforms on {cores} threads (scipy.fft), measured once",
+                               "single_thread": {"value": cv, "unit": UNIT, "cores": 1,
+                                                 "sample": f"2 forward + 2 adjoint Jacobi stages at 128^3 "
+                                                           f"({secs:.1f} s, numpy.fft), scaled by 2*nt/2 = 10 "
+                                                           f"to one Hv"}}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

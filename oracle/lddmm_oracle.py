@@ -48,6 +48,18 @@ import numpy as np
 
 AXES = (-3, -2, -1)
 
+# FFT backend: numpy's pocketfft on one thread (default), or scipy.fft with
+# worker threads (the same transform, used to time the oracle on several
+# host cores).
+_FFT_WORKERS = None
+
+
+def set_fft_workers(workers=None):
+    """Route the oracle's transforms through scipy.fft with `workers`
+    threads; None restores numpy.fft."""
+    global _FFT_WORKERS
+    _FFT_WORKERS = workers
+
 
 # ---------------------------------------------------------------------------
 # Grid, symbols and spectral operators (Sec. 2.1: L = (Id - alpha Lap)^s)
@@ -102,9 +114,15 @@ class Grid:
 
     # transforms --------------------------------------------------------
     def fwd(self, f):
+        if _FFT_WORKERS:
+            import scipy.fft
+            return scipy.fft.rfftn(f, axes=AXES, workers=_FFT_WORKERS)
         return np.fft.rfftn(f, axes=AXES)
 
     def inv(self, F):
+        if _FFT_WORKERS:
+            import scipy.fft
+            return scipy.fft.irfftn(F, s=self.n, axes=AXES, workers=_FFT_WORKERS)
         return np.fft.irfftn(F, s=self.n, axes=AXES)
 
     # operators on real fields -----------------------------------------
@@ -316,10 +334,11 @@ class Trajectory:
     grad_m1: Optional[np.ndarray] = None
 
 
-def shoot(g: Grid, v0, nt, I0=None, kind="cubic"):
+def shoot(g: Grid, v0, nt, I0=None, kind="cubic", transport=True):
     """Forward geodesic shooting of P v0 by Heun steps of the EPDiff
     equation, with SL transport of the inverse map and the final warp
-    m(1) = I0(x+u)."""
+    m(1) = I0(x+u).  ``transport=False`` keeps u = 0 and m(1) = I0 (the
+    EPDiff states alone; used to time the sweeps without the transport)."""
     dt = 1.0 / nt
     v = [g.P(v0)]
     vstar = []
@@ -330,11 +349,12 @@ def shoot(g: Grid, v0, nt, I0=None, kind="cubic"):
         r2 = epdiff_rhs(g, vs)
         v.append(v[k] + 0.5 * dt * (r1 + r2))
         vstar.append(vs)
-        u = sl_map_step(g, u, v[k], v[k + 1], dt, kind)
+        if transport:
+            u = sl_map_step(g, u, v[k], v[k + 1], dt, kind)
     kin = [g.dot(g.L(vk), vk) for vk in v]
     tr = Trajectory(nt=nt, v=v, vstar=vstar, u=u, kinetic=kin)
     if I0 is not None:
-        tr.m1 = warp(g, I0, u, kind)
+        tr.m1 = warp(g, I0, u, kind) if transport else np.array(I0, dtype=np.float64)
         tr.grad_m1 = g.grad(tr.m1)
     return tr
 

@@ -178,6 +178,46 @@ template <int P> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(P) : "memory");
 }
 
+// sym_apply for an element of a line along axis AX whose index on that axis
+// is p: the line axis' kappa^2 and derivative tables are read from shared
+// memory (ksqs, dks), the fixed axes' entries from the global tables (the
+// same for every element of the line).  Same arithmetic as sym_apply.
+template <class T, int AX>
+__device__ __forceinline__ cpx<T> sym_apply_line(const SymT<T>& sy, const SpecTabs<T>& tb, const T* ksqs,
+                                                 const T* dks, int k0, int k1, int k2, cpx<T> v) {
+    if (sy.mask) {
+        const bool out0 = k0 > tb.kcut[0] && k0 < tb.n[0] - tb.kcut[0];
+        const bool out1 = k1 > tb.kcut[1] && k1 < tb.n[1] - tb.kcut[1];
+        if (out0 || out1 || k2 > tb.kcut[2]) return mk((T)0, (T)0);
+    }
+    T f = sy.scale;
+    if (sy.lpow != 0) {
+        const T q0 = AX == 0 ? ksqs[k0] : tb.ksq[0][k0];
+        const T q1 = AX == 1 ? ksqs[k1] : tb.ksq[1][k1];
+        const T base = (T)1 + tb.alpha * (q0 + q1 + tb.ksq[2][k2]);
+        const int e = tb.s * (sy.lpow > 0 ? sy.lpow : -sy.lpow);
+        T pw;
+        if (e == 2) {
+            pw = base * base;
+        } else if (e == 4) {
+            pw = base * base;
+            pw = pw * pw;
+        } else {
+            pw = (T)1;
+            for (int q = 0; q < e; ++q) pw *= base;
+        }
+        f = sy.lpow > 0 ? f * pw : sym_div(f, pw);
+    }
+    if (sy.deriv >= 0) {
+        T dk;
+        if (sy.deriv == AX) dk = dks[AX == 0 ? k0 : k1];
+        else dk = tb.dk[sy.deriv][sy.deriv == 0 ? k0 : (sy.deriv == 1 ? k1 : k2)];
+        const T d = dk * f;
+        return mk(-d * v.y, d * v.x);
+    }
+    return mk(f * v.x, f * v.y);
+}
+
 // ---------------------------------------------------------------- C2C passes
 // Persistent blocks walk the (tile, job) work items of the launch; every
 // input tile of an item is a "load unit".  The next unit is copied into the
@@ -203,7 +243,19 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
     cpx<T>* const stage0 = (cpx<T>*)smem_raw;
     cpx<T>* b0 = stage0 + 2 * G::TILE;
     cpx<T>* b1 = b0 + TL * SIdx<T, N, MAP>::LP;
-    const cpx<T>* tw = (const cpx<T>*)pp.ax.tw;
+    // the axis' twiddles and symbol tables in shared memory (the first
+    // barrier of the main loop orders these stores before their reads)
+    cpx<T>* const tws = b1 + TL * SIdx<T, N, MAP>::LP;
+    T* const ksqs = (T*)(tws + N);
+    T* const dks = ksqs + N;
+    {
+        const cpx<T>* tw = (const cpx<T>*)pp.ax.tw;
+        for (int i = threadIdx.x; i < N; i += FAST_THREADS) {
+            tws[i] = ldg(tw + i);
+            ksqs[i] = pp.tabs.ksq[AXIS][i];
+            dks[i] = pp.tabs.dk[AXIS][i];
+        }
+    }
     const int n0 = pp.n0, n1 = pp.n1, n2h = pp.n2h;
     const int nitems = ntiles * pp.njobs;
     int c, t;
@@ -337,9 +389,10 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
 #pragma unroll
                     for (int m = 0; m < E; ++m) {
                         const int p = t + TPL * m;
-                        x[m] = sym_apply(sy, pp.tabs, AXIS == 0 ? p : k0b, AXIS == 1 ? p : k1b, k2b, acc[m]);
+                        x[m] = sym_apply_line<T, AXIS>(sy, pp.tabs, ksqs, dks, AXIS == 0 ? p : k0b,
+                                                       AXIS == 1 ? p : k1b, k2b, acc[m]);
                     }
-                    fast_fft<T, N, MAP>(x, b0, b1, c, t, tw, +1);
+                    fast_fft<T, N, MAP, true>(x, b0, b1, c, t, tws, +1);
                     if (valid) {
                         cpx<T>* ob = (cpx<T>*)job.out[o] + gidx(t);
                         const int sm = AXIS == 1 ? TPL : TPL * n1;  // element step between m
@@ -353,12 +406,13 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
 #pragma unroll
             for (int m = 0; m < E; ++m) x[m] = valid ? tile[at(t + TPL * m)] : mk((T)0, (T)0);
             __syncthreads();
-            fast_fft<T, N, MAP>(x, b0, b1, c, t, tw, -1);
+            fast_fft<T, N, MAP, true>(x, b0, b1, c, t, tws, -1);
             const SymT<T> sy = job.isym[q];
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const int p = t + TPL * m;
-                const cpx<T> v = sym_apply(sy, pp.tabs, AXIS == 0 ? p : k0b, AXIS == 1 ? p : k1b, k2b, x[m]);
+                const cpx<T> v = sym_apply_line<T, AXIS>(sy, pp.tabs, ksqs, dks, AXIS == 0 ? p : k0b,
+                                                         AXIS == 1 ? p : k1b, k2b, x[m]);
                 acc[m] = q == 0 ? v : acc[m] + v;
             }
             if (last && valid) {
@@ -690,8 +744,9 @@ template <class T, int N> constexpr size_t fast_axis2p_smem() {
 
 template <class T, int N> constexpr size_t fast_c2c_smem(int axis) {
     return ((size_t)2 * C2CGeom<T, N, 1>::TILE +
-            (size_t)2 * (FAST_THREADS / (N / FastPlan<N>::E)) * (axis == 1 ? SIdx<T, N, 1>::LP : SIdx<T, N, 0>::LP)) *
-           sizeof(cpx<T>);
+            (size_t)2 * (FAST_THREADS / (N / FastPlan<N>::E)) * (axis == 1 ? SIdx<T, N, 1>::LP : SIdx<T, N, 0>::LP) +
+            (size_t)N) * sizeof(cpx<T>) +
+           (size_t)2 * N * sizeof(T);  // twiddles, kappa^2 and derivative tables of the axis
 }
 template <class T, int N> constexpr size_t fast_axis2_smem() {
     constexpr int TL = FAST_THREADS / (N / FastPlan<N>::E);

@@ -8,7 +8,9 @@ from the FP64 oracle alone).
   decisions, energies and final metrics;
 * GPU: on the 128^3 benchmark workload, in the configuration the benchmark
   times (FP32 form, nt = 10), the V gradient and the V Hessian-vector
-  product match the oracle at 2048 stored sample points.
+  product match the oracle at 2048 stored sample points and on stored
+  complete planes along each axis; the target rebuilt on the GPU in FP64 is
+  checked against the oracle's stored samples first.
 """
 import json
 import os
@@ -90,7 +92,12 @@ def test_gpu_bench128_gradient_and_hv_at_sampled_points():
         m1 = h64.new_img()
         h64.lddmm_shoot(torch.tensor(v0t, dtype=f64, device="cuda"), torch.tensor(P, dtype=f64, device="cuda"), m1)
         h64.lddmm_synchronize()
-        I1 = m1.cpu().numpy() + e1
+        m1t = m1.cpu().numpy()
+    # the rebuilt target is the oracle's (stored samples and norm) to 1e-9
+    rel = lambda a, b: float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+    assert rel(m1t.ravel()[idx % m1t.size], ref["m1_true"]) < 1e-9
+    assert abs(np.linalg.norm(m1t) - ref["m1_true_l2"]) < 1e-9 * ref["m1_true_l2"]
+    I1 = m1t + e1
     prm = pkg.default_params(alpha=0.005, nt=10, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_F32)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=f32, device="cuda")
     with pkg.Handle(n, prm) as h:
@@ -99,9 +106,15 @@ def test_gpu_bench128_gradient_and_hv_at_sampled_points():
         h.lddmm_hessvec(T(d), hv)
         h.lddmm_synchronize()
         gn, hn = grad.double().cpu().numpy(), hv.double().cpu().numpy()
-    rel = lambda a, b: float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
     assert abs(e[0] - ref["E"]) < 1e-5 * ref["E"]
     assert rel(gn.ravel()[idx], ref["grad_V"]) < 1e-5
     assert rel(hn.ravel()[idx], ref["hv_V"]) < 1e-5
     assert abs(np.linalg.norm(gn) - ref["grad_V_l2"]) < 1e-5 * ref["grad_V_l2"]
     assert abs(np.linalg.norm(hn) - ref["hv_V_l2"]) < 1e-5 * ref["hv_V_l2"]
+    # complete planes across every tile of the other two axes
+    planes = np.load(os.path.join(HERE, "golden", "bench128_planes.npz"))
+    mg = _mg()
+    for name, field, cuts in (("hv_V", hn, mg.BENCH128_HV_PLANES), ("grad_V", gn, mg.BENCH128_GRAD_PLANES)):
+        for axis, i in cuts:
+            want = planes[f"{name}_axis{axis}_{i}"]
+            assert rel(np.take(field, i, axis=1 + axis), want) < 1e-5, (name, axis, i)

@@ -263,3 +263,60 @@ def test_band_limited_grids_vs_oracle(pkg, prec, n, monkeypatch):
     assert rel(host(e1g), want["tan"][0]) < tol
     assert rel(host(x1g), want["tan"][1]) < tol
     assert rel(host(a0g), want["adj"]) < tol
+
+
+def test_brain_shaped_grid_metric_full_array_and_shoot_vs_oracle(pkg):
+    """The 256x300x256 grid of the brain-shaped workload: its n1 = 300 axis
+    (2^2 3 5^2) runs the runtime-radix passes.  K and L on a field against
+    the oracle over the whole array (FP32 1e-5, FP64 1e-10); the FP32 shoot
+    (nt = 2, FP32 states) against the oracle's stored samples, complete
+    planes, norms and kinetic energies (tests/golden/make_golden.py config3);
+    the precision form's shoot (bfloat16 states, checkpointed) reported
+    against the same values at its own tolerance (reading C14)."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    n, nt, alpha = mg.C3_N, mg.C3_NT, mg.C3_ALPHA
+    g = O.Grid(n, alpha=alpha)
+    f = synth.band_limited_field(n, synth.rng_for(301), 10.0, 3) + 0.05 * synth.rng_for(302).standard_normal((3,) + n)
+    for prec, tol in (("f64", 1e-10), ("f32", 1e-5)):
+        dtype, cd = DT[prec]
+        with pkg.Handle(n, pkg.default_params(alpha=alpha, nt=1, compute_dtype=cd, state_dtype=cd)) as h:
+            x = dev(f, dtype)
+            out = torch.empty_like(x)
+            h.lddmm_apply_metric(x, out, -1)
+            h.lddmm_synchronize()
+            assert rel(host(out), g.K(f)) < tol, prec
+            h.lddmm_apply_metric(x, out, 1)
+            h.lddmm_synchronize()
+            assert rel(host(out), g.L(f)) < tol, prec
+            del x, out
+    with open(os.path.join(here, "golden", "config3_256x300x256.json")) as fh:
+        ref = json.load(fh)
+    planes = np.load(os.path.join(here, "golden", "config3_planes.npz"))
+    I0, v0t = mg.config3_inputs()
+    idx = mg.config3_sample_idx()
+    assert [int(i) for i in idx] == ref["idx"]
+    f32 = torch.float32
+    for states, ckpt, tol in ((pkg.LDDMM_F32, 1, 1e-5), (pkg.LDDMM_BF16, 2, 2e-2)):
+        prm = pkg.default_params(alpha=alpha, nt=nt, compute_dtype=pkg.LDDMM_F32, state_dtype=states,
+                                 checkpoint_every=ckpt)
+        with pkg.Handle(n, prm) as h:
+            m1, u1 = h.new_img(), h.new_vec()
+            kin = h.lddmm_shoot(dev(v0t, f32), dev(I0, f32), m1, u1, kinetic=True)
+            h.lddmm_synchronize()
+            un, mn = host(u1), host(m1)
+        assert rel(un.ravel()[idx], ref["u1"]) < tol, (states, rel(un.ravel()[idx], ref["u1"]))
+        assert rel(mn.ravel()[idx % mn.size], ref["m1"]) < tol
+        assert abs(np.linalg.norm(un) - ref["u1_l2"]) < tol * ref["u1_l2"]
+        assert abs(np.linalg.norm(mn) - ref["m1_l2"]) < tol * ref["m1_l2"]
+        assert np.allclose(kin, ref["kinetic"], rtol=tol, atol=0)
+        if states == pkg.LDDMM_F32:
+            for axis, i in mg.C3_U_PLANES:
+                assert rel(np.take(un, i, axis=1 + axis), planes[f"u1_axis{axis}_{i}"]) < tol, (axis, i)
+            for axis, i in mg.C3_M_PLANES:
+                assert rel(np.take(mn, i, axis=axis), planes[f"m1_axis{axis}_{i}"]) < tol, (axis, i)

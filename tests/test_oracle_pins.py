@@ -658,3 +658,19 @@ def test_gauss_newton_armijo_acceptance():
             assert O.energy(g, p, v + 2 * eps * x, I0, I1)[0] > E + c1 * 2 * eps * slope
         v = v + eps * x
     assert rel(v, rep.v0) < 1e-13
+
+
+def test_threaded_fft_backend_gives_the_same_operators():
+    """The scipy.fft backend with worker threads (used only to time the
+    oracle on several cores) computes the same spectral operators as
+    numpy.fft, to rounding."""
+    g = O.Grid((12, 10, 14), alpha=0.05)
+    v = rough(g.n, 80)
+    ref = (g.K(v), g.P(v), g.grad(v[0]))
+    O.set_fft_workers(4)
+    try:
+        got = (g.K(v), g.P(v), g.grad(v[0]))
+    finally:
+        O.set_fft_workers(None)
+    for a, b in zip(got, ref):
+        assert rel(a, b) < 1e-14
