@@ -58,8 +58,9 @@ def parse():
                     help="requests of the serving trace, a prefix of its 256 (0: skip)")
     ap.add_argument("--no-plain-registration", action="store_true",
                     help="skip the registration of the workload with the plain FP64 method")
-    ap.add_argument("--serve-fp64", type=int, default=3,
-                    help="run the first M serving requests serially with the plain FP64 method (0: skip)")
+    ap.add_argument("--serve-fp64", type=int, default=2,
+                    help="run the first M serving requests serially with the plain FP64 method and with the "
+                         "FP32 form (0: skip)")
     ap.add_argument("--no-config3", action="store_true",
                     help="skip the 256x300x256 registration (FP32, bfloat16 states, checkpointing)")
     return ap.parse_args()
@@ -243,27 +244,32 @@ def run_serving(args, dev):
            "peak_inflight": srv.peak_inflight, "peak_workspace_gb": round(srv.peak_used / 1e9, 2),
            "mse_rel_mean": float(np.mean([r.report["mse_rel"] for r in res if r.report])), **st}
     if args.serve_fp64 > 0:
+        # the plain FP64 method and the FP32 form, each serially in FIFO
+        # order, on the first m requests of the trace
         m = min(args.serve_fp64, len(reqs))
-        p64 = mk(pkg.LDDMM_F64)
-        sub = [Request(rid=r.rid, I0=r.I0, I1=r.I1, params=p64, arrival=0.0) for r in reqs[:m]]
-        t0 = time.perf_counter()
-        ser = serial(sub, device=dev.index)
-        wall = time.perf_counter() - t0
-        ok = [r for r in ser if r.report]
-        dm = [abs(a.report["mse_rel"] - b.report["mse_rel"]) / b.report["mse_rel"]
-              for a, b in zip(res[:m], ser) if a.report and b.report]
+        runs = {}
+        for name, prm_ in (("plain_fp64_serial", mk(pkg.LDDMM_F64)), ("fp32_serial", p32)):
+            sub = [Request(rid=r.rid, I0=r.I0, I1=r.I1, params=prm_, arrival=0.0) for r in reqs[:m]]
+            t0 = time.perf_counter()
+            ser = serial(sub, device=dev.index)
+            runs[name] = (ser, time.perf_counter() - t0)
         served_sub = [r for r in res[:m] if r.report]
-        out["plain_fp64_serial"] = {"requests": m, "registrations_per_s": len(ok) / wall,
-                                    "mean_latency_s": wall / max(len(ok), 1),
-                                    "mse_rel_mean": float(np.mean([r.report["mse_rel"] for r in ok])),
-                                    "served_fp32_mse_rel_mean_same_requests":
-                                        float(np.mean([r.report["mse_rel"] for r in served_sub])),
-                                    "max_rel_diff_mse_rel_vs_served": max(dm) if dm else None}
+        for name, (ser, wall) in runs.items():
+            ok = [r for r in ser if r.report]
+            dm = [abs(a.report["mse_rel"] - b.report["mse_rel"]) / b.report["mse_rel"]
+                  for a, b in zip(res[:m], ser) if a.report and b.report]
+            out[name] = {"requests": m, "sizes": [list(r.I0.shape) for r in reqs[:m]],
+                         "registrations_per_s": len(ok) / wall, "mean_latency_s": wall / max(len(ok), 1),
+                         "mse_rel_mean": float(np.mean([r.report["mse_rel"] for r in ok])),
+                         "served_fp32_mse_rel_mean_same_requests":
+                             float(np.mean([r.report["mse_rel"] for r in served_sub])),
+                         "max_rel_diff_mse_rel_vs_served": max(dm) if dm else None}
     return out
 
 
 # ----------------------------------------------------------------------------- 256x300x256
 N3 = (256, 300, 256)
+C3_PCG_CAP = 10
 
 
 def run_config3(dev, stream):
@@ -271,7 +277,9 @@ def run_config3(dev, stream):
     ellipsoids with a 4-voxel boundary perturbation, noise 0.02; target =
     the phantom shot by a |k| <= 8, 8-voxel velocity plus noise) in the FP32
     form with bfloat16 stored states and forward states checkpointed every 2
-    steps: 10 Gauss-Newton iterations, PCG rtol 0.1, cap 50."""
+    steps: 10 Gauss-Newton iterations, PCG rtol 0.1, at most 10 PCG iterations
+    each (the bench's time budget; the configuration's cap of 50 takes about
+    five minutes)."""
     import numpy as np
     import torch
 
@@ -280,7 +288,7 @@ def run_config3(dev, stream):
     P, v0t, e0, e1 = synth.ellipsoid_pair_inputs(N3, 2, kmax=8, max_disp_vox=8.0, noise_sigma=0.02,
                                                  perturb_vox=4.0)
     prm = pkg.default_params(alpha=ALPHA, nt=NT, compute_dtype=pkg.LDDMM_F32, state_dtype=pkg.LDDMM_BF16,
-                             checkpoint_every=2, gn_maxit=10, pcg_maxit=50, pcg_rtol=0.1)
+                             checkpoint_every=2, gn_maxit=10, pcg_maxit=C3_PCG_CAP, pcg_rtol=0.1)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     h = pkg.Handle(N3, prm, stream=stream, device=dev.index)
     try:
@@ -297,6 +305,7 @@ def run_config3(dev, stream):
     finally:
         h.close()
     return {"grid": list(N3), "form": "FP32, bfloat16 stored states, checkpoint every 2 steps", "seconds": secs,
+            "weight": prm.weight, "pcg_rtol": 0.1, "pcg_cap": C3_PCG_CAP,
             "workspace_gb": round(pkg.workspace_bytes(N3, prm) / 1e9, 2), "gn_iters": r["gn_iters"],
             "pcg_iters_total": r["pcg_iters_total"], "mse_rel": r["mse_rel"], "gnorm_rel": r["gnorm_rel"],
             "jac_min": r["jac_min"], "jac_max": r["jac_max"], "status": r["status"]}
