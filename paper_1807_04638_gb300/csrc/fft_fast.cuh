@@ -116,6 +116,19 @@ template <class T, int N, int MAP> struct SIdx {
     }
 };
 
+// Barrier of a line's exchanges.  Only the TPL threads of a line touch its
+// exchange tiles; with MAP 1 (t fastest) they are consecutive threads of one
+// warp (TPL divides 32), so a warp barrier suffices, while with MAP 0 they
+// are spread over the block.
+template <int MAP, int TPL> __device__ __forceinline__ void line_sync() {
+    if constexpr (MAP == 1) {
+        static_assert(32 % TPL == 0, "a line's threads must lie in one warp");
+        __syncwarp();
+    } else {
+        __syncthreads();
+    }
+}
+
 // TWS: the twiddle table tw is in shared memory (else global, read through
 // the read-only cache)
 template <class T, int N, int E, int TPL, int RADS, int S, int NS, int MAP, bool TWS = false>
@@ -151,7 +164,7 @@ __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* 
         }
     }
     if constexpr (!LAST) {
-        __syncthreads();
+        line_sync<MAP, TPL>();
 #pragma unroll
         for (int m = 0; m < E; ++m) x[m] = b0[SIdx<T, N, MAP>::at(c, t + TPL * m)];
         fast_stages<T, N, E, TPL, RADS, S + 1, NS * R, MAP, TWS>(x, b1, b0, c, t, tw, dir);
@@ -162,7 +175,7 @@ template <class T, int N, int MAP, bool TWS = false>
 __device__ __forceinline__ void fast_fft(cpx<T> (&x)[FastPlan<N>::E], cpx<T>* b0, cpx<T>* b1, int c, int t,
                                          const cpx<T>* tw, int dir) {
     constexpr int E = FastPlan<N>::E;
-    __syncthreads();  // the tiles may still be read by the previous transform
+    line_sync<MAP, N / E>();  // the line's tiles may still be read by its previous transform
     fast_stages<T, N, E, N / E, FastPlan<N>::RADS, 0, 1, MAP, TWS>(x, b0, b1, c, t, tw, dir);
 }
 
@@ -704,6 +717,10 @@ __global__ void __launch_bounds__(FAST_THREADS, A2P_BLOCKS) k_fast_axis2p(const 
             const T* Sr = (const T*)S + (2 * c) * N + t;  // row pair (2c, 2c + 1) of the tile
 #pragma unroll
             for (int m = 0; m < E; ++m) x[m] = mk(Sr[TPL * m], Sr[N + TPL * m]);
+            // the exchange tile is the stage buffer itself: with a padded line
+            // pitch a line's exchange region overlaps the next line's rows, so
+            // every line must have read its rows first
+            if constexpr (SIdx<T, N, 1>::LP != N) __syncthreads();
             fast_fft<T, N, 1>(x, b0, b1, c, t, tw, -1);
             // stage the packed spectrum to pair Z_k with Z_{N-k}
             __syncthreads();

@@ -327,10 +327,13 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
             for (int m = 0; m < E; ++m) acc[f][m] = 0.f;
         // ---------------- inverse lines
         for (int l = 0; l < NLI; ++l) {
+            // this line's inputs are complete and visible, and every warp is
+            // done with the other buffer (read by the previous line) before
+            // the next line's copies go there
+            cp_async_wait<0>();
+            __syncthreads();
             const int nl = l + 1 < NLI ? l + 1 : 0;
             issue(l + 1 < NLI ? tile : tile + gridDim.x, nl, sb ^ 1);
-            cp_async_wait<1>();
-            __syncthreads();
             const cpx<float>* const stg = stage0 + sb * G::STG;
             if constexpr (KIND == 0) {
                 prefetch_line_fields<SS, N, TL>(tile_states, a.npts, l / 6, l % 6);
