@@ -342,8 +342,8 @@ struct FusedPass {
     static bool has(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
     static int tile_rows(int n) { return FAST_THREADS / (n / 8); }
     template <int N, class SS, int KIND> static bool go(const FusedArgs& a, cudaStream_t st, bool set_attr) {
-        constexpr size_t sm = KIND == 0 ? FusedGeom<N>::SMEM0 : FusedGeom<N>::SMEM1;
-        if (set_attr) return raise_smem_limit(k_fused_stage<SS, N, KIND>, sm);
+        if (set_attr) return raise_smem_limit(k_fused_stage<SS, N, KIND>, FusedGeom<N>::smem(KIND, N / 2 + 1));
+        const size_t sm = FusedGeom<N>::smem(KIND, a.nb2);
         k_fused_stage<SS, N, KIND><<<persistent_grid(a.ntiles, FUSED_BLOCKS), FAST_THREADS, sm, st>>>(a);
         return true;
     }

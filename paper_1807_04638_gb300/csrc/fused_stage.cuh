@@ -71,7 +71,6 @@ template <int N> struct FusedGeom {
     static constexpr int TL = FAST_THREADS / TPL;  // rows per tile
     static constexpr int NH = N / 2 + 1;
     static constexpr int SP = TL + 2;              // staged plane pitch (complex; 16-byte rows)
-    static constexpr int STG = 2 * NH * SP;        // one stage buffer: two inputs
     static constexpr int XT = TL * SIdx<float, N, 1>::LP;  // one exchange tile
     static constexpr int PH = (NH % 2 == 0) ? NH + 1 : NH;  // H pitch
     static constexpr int HS = 2 * TL * PH;         // two unpacked outputs
@@ -82,8 +81,18 @@ template <int N> struct FusedGeom {
     static constexpr int RP = N + 16;
     static constexpr int FS = TL * RP + 16;
     static constexpr int TWD = N + (NH + 1) / 2;   // twiddles, then kappa_2 (complex slots)
-    static constexpr size_t SMEM0 = (size_t)(2 * STG + 2 * XT + HS + TWD) * sizeof(cpx<float>);
-    static constexpr size_t SMEM1 = SMEM0 + (size_t)2 * FS * sizeof(float);
+    // Shared memory: two stage buffers, each the band planes k2 < nb2 of two
+    // inputs and at least HS (the forward lines' unpacked outputs H live in
+    // the buffer that no copy targets then), two exchange tiles, the tables,
+    // and for the adjoint the hand-off rows.  Sized at launch from nb2: what
+    // it leaves of the SM's 256 KB serves as L1 for the prefetched states.
+    static __host__ __device__ constexpr int stage_elems(int nb2) {
+        return 2 * nb2 * SP > HS ? 2 * nb2 * SP : HS;
+    }
+    static constexpr size_t smem(int kind, int nb2) {
+        return (size_t)(2 * stage_elems(nb2) + 2 * XT + TWD) * sizeof(cpx<float>) +
+               (kind == 1 ? (size_t)2 * FS * sizeof(float) : 0);
+    }
     static_assert(TL % 2 == 0, "the adjoint pairs the rows of a tile");
 };
 
@@ -131,8 +140,9 @@ __device__ __forceinline__ int line_field(int c, int ty, int q) {
 
 // Bring the state rows of a tile that line (c, type) reads into L1 (one
 // prefetch per 128-byte line), ahead of the loads of its products, so that
-// those loads do not wait on L2.
-template <class SS, int N, int TL>
+// those loads do not wait on L2; with L2 = true, into L2 only (a line
+// further ahead, so that the L1 prefetch does not wait on DRAM).
+template <class SS, int N, int TL, bool L2 = false>
 __device__ __forceinline__ void prefetch_line_fields(const SS* tile_states, unsigned npts, int c, int ty) {
     // the tile's rows of one field are contiguous: PER cache lines
     constexpr int PER = (int)(TL * N * sizeof(SS) / 128);
@@ -141,7 +151,8 @@ __device__ __forceinline__ void prefetch_line_fields(const SS* tile_states, unsi
         const int f = line_field(c, ty, i / PER);
         if (f < 0) break;
         const char* p = (const char*)(tile_states + (size_t)f * npts) + (size_t)(i % PER) * 128;
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+        if constexpr (L2) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+        else asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
     }
 }
 
@@ -275,12 +286,13 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
     constexpr int E = G::E, TPL = G::TPL, TL = G::TL, NH = G::NH, SP = G::SP, PH = G::PH, RP = G::RP, FS = G::FS;
     constexpr int NLI = KIND == 0 ? 18 : 3;   // inverse lines per row (tangent) / rounds (adjoint)
     constexpr int NLO = KIND == 0 ? 3 : 18;   // forward lines per row / rounds
+    constexpr int NBUF = 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<float>* const stage0 = (cpx<float>*)smem_raw;  // buffers stage0 + sb * STG
-    cpx<float>* const b0 = stage0 + 2 * G::STG;
+    const int STG = G::stage_elems(a.nb2);              // one stage buffer (complex)
+    cpx<float>* const stage0 = (cpx<float>*)smem_raw;  // buffers stage0 + sb * STG, sb < NBUF
+    cpx<float>* const b0 = stage0 + NBUF * STG;
     cpx<float>* const b1 = b0 + G::XT;
-    cpx<float>* const H = b1 + G::XT;
-    cpx<float>* const tws = H + G::HS;                  // twiddles
+    cpx<float>* const tws = b1 + G::XT;                 // twiddles
     float* const dks = (float*)(tws + N);              // kappa_2 (Nyquist zeroed)
     float* const R = (float*)(tws + G::TWD);           // adjoint: two real fields of the tile's rows
     const int c = threadIdx.x / TPL, t = threadIdx.x % TPL;
@@ -294,14 +306,14 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
             fused_line_inputs<KIND>(l, i0, i1);
             const int nin = i1 >= 0 ? 2 : 1;  // staged inputs
             const int per = nb2 * G::CPK;
-            cpx<float>* dst = stage0 + buf * G::STG;
+            cpx<float>* dst = stage0 + buf * STG;
             const size_t r0 = (size_t)tile * TL;
             for (int i = threadIdx.x; i < nin * per; i += FAST_THREADS) {
                 const int qq = i >= per;
                 const int rem = i - qq * per;
                 const int k = rem / G::CPK, ch = rem % G::CPK;
                 const cpx<float>* src = a.in[qq ? i1 : i0] + (size_t)k * rows + r0;
-                cp_async16(dst + qq * NH * SP + k * SP + 2 * ch, src + 2 * ch);
+                cp_async16(dst + qq * nb2 * SP + k * SP + 2 * ch, src + 2 * ch);
             }
         }
         cp_async_commit();
@@ -311,7 +323,21 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
     if (tile >= ntiles) return;
     for (int i = threadIdx.x; i < N; i += FAST_THREADS) tws[i] = ldg(a.tw + i);
     for (int i = threadIdx.x; i < NH; i += FAST_THREADS) dks[i] = __ldg(a.dk2 + i);
-    issue(tile, 0, 0);
+    // the (tile, line) units of this block in order; the first NBUF - 1 go in
+    // flight now, and each line sends the one NBUF - 1 ahead
+    auto ahead = [&](int tl, int l, int d, int& tl2, int& l2) {
+        tl2 = tl;
+        l2 = l + d;
+        while (l2 >= NLI) {
+            l2 -= NLI;
+            tl2 += gridDim.x;
+        }
+    };
+    for (int d = 0; d < NBUF - 1; ++d) {
+        int tl2, l2;
+        ahead(tile, 0, d, tl2, l2);
+        issue(tl2, l2, d);
+    }
     int sb = 0;
     const SS* const states = (const SS*)a.states;
     cpx<float> x[E];
@@ -330,18 +356,21 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
             // this line's inputs are complete and visible, and every warp is
             // done with the other buffer (read by the previous line) before
             // the next line's copies go there
-            cp_async_wait<0>();
+            cp_async_wait<NBUF - 2>();
             __syncthreads();
-            const int nl = l + 1 < NLI ? l + 1 : 0;
-            issue(l + 1 < NLI ? tile : tile + gridDim.x, nl, sb ^ 1);
-            const cpx<float>* const stg = stage0 + sb * G::STG;
+            {
+                int tl2, l2;
+                ahead(tile, l, NBUF - 1, tl2, l2);
+                issue(tl2, l2, sb == 0 ? NBUF - 1 : sb - 1);
+            }
+            const cpx<float>* const stg = stage0 + sb * STG;
             if constexpr (KIND == 0) {
                 prefetch_line_fields<SS, N, TL>(tile_states, a.npts, l / 6, l % 6);
                 // two fields of this line group's row: (in[i0], D2 in[i0]) or (in[i0], in[i1])
                 int i0, i1;
                 fused_line_inputs<KIND>(l, i0, i1);
                 const cpx<float>* SA = stg + c;
-                const cpx<float>* SB = SA + NH * SP;
+                const cpx<float>* SB = SA + nb2 * SP;
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
                     const int k = t + TPL * m;
@@ -370,7 +399,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
             } else {
                 if (l == NLI - 1) prefetch_line_fields<SS, N, TL>(tile_states, a.npts, 0, 0);
                 // one field (input q of the line) on a pair of rows
-                const cpx<float>* SA = stg + q * NH * SP + 2 * rp;
+                const cpx<float>* SA = stg + q * nb2 * SP + 2 * rp;
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
                     const int k = t + TPL * m;
@@ -428,9 +457,12 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                     }
                 }
             }
-            sb ^= 1;
+            sb = sb + 1 == NBUF ? 0 : sb + 1;
         }
         // ---------------- forward lines
+        // the unpacked outputs go to the stage buffer that no copy targets
+        // until the next tile's first line (sb holds that line's inputs)
+        cpx<float>* const H = stage0 + (sb ^ 1) * STG;
         for (int f = 0; f < NLO; ++f) {
             if constexpr (KIND == 0) {
 #pragma unroll
