@@ -129,8 +129,43 @@ template <int MAP, int TPL> __device__ __forceinline__ void line_sync() {
     }
 }
 
-// TWS: the twiddle table tw is in shared memory (else global, read through
-// the read-only cache)
+// Per-stage twiddle tables in shared memory: stage S >= 1 (radix R, NS) keeps
+// w^(k r N / (NS R)) at (r - 1) NS + k for k < NS, 1 <= r < R, so that the
+// threads of a line read consecutive (or equal) entries: no bank conflicts.
+template <int N, int S> struct StageTw {
+    static constexpr int RADS = FastPlan<N>::RADS;
+    static __host__ __device__ constexpr int radix(int s) { return (RADS >> (4 * s)) & 0xF; }
+    static __host__ __device__ constexpr int ns(int s) { return s == 0 ? 1 : ns(s - 1) * radix(s - 1); }
+    static __host__ __device__ constexpr int off(int s) {
+        return s <= 1 ? 0 : off(s - 1) + (radix(s - 1) - 1) * ns(s - 1);
+    }
+    static constexpr int R = radix(S), NS = ns(S), OFF = off(S);
+};
+template <int N> struct TwTable {
+    static __host__ __device__ constexpr int nstages() {
+        int n = 0;
+        for (int r = FastPlan<N>::RADS; r; r >>= 4) ++n;
+        return n;
+    }
+    static constexpr int SIZE = StageTw<N, 15>::off(nstages());  // entries of all stages
+};
+// fill the per-stage tables from the twiddle table tw (e^{-2 pi i t / N}); all
+// threads of the block call it
+template <class T, int N>
+__device__ __forceinline__ void fill_stage_twiddles(cpx<T>* tws, const cpx<T>* tw) {
+    using ST = StageTw<N, 15>;
+    constexpr int NST = TwTable<N>::nstages();
+    for (int i = threadIdx.x; i < TwTable<N>::SIZE; i += blockDim.x) {
+        int s = 1;
+        while (s + 1 < NST && i >= ST::off(s + 1)) ++s;
+        const int ns = ST::ns(s), R = ST::radix(s);
+        const int j = i - ST::off(s), r = j / ns + 1, k = j % ns;
+        tws[i] = ldg(tw + k * r * (N / (ns * R)));
+    }
+}
+
+// TWS: the twiddles are the per-stage tables in shared memory (else the
+// global table, read through the read-only cache)
 template <class T, int N, int E, int TPL, int RADS, int S, int NS, int MAP, bool TWS = false>
 __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* b1, int c, int t, const cpx<T>* tw,
                                             int dir) {
@@ -147,7 +182,7 @@ __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* 
         for (int r = 0; r < R; ++r) {
             cpx<T> a = x[b + B * r];
             if (NS > 1 && r > 0) {
-                cpx<T> w = TWS ? tw[k * r * (N / (NS * R))] : ldg(&tw[k * r * (N / (NS * R))]);
+                cpx<T> w = TWS ? tw[StageTw<N, S>::OFF + (r - 1) * NS + k] : ldg(&tw[k * r * (N / (NS * R))]);
                 if (dir > 0) w.y = -w.y;
                 a = a * w;
             }
@@ -261,13 +296,11 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
     cpx<T>* const tws = b1 + TL * SIdx<T, N, MAP>::LP;
     T* const ksqs = (T*)(tws + N);
     T* const dks = ksqs + N;
-    {
-        const cpx<T>* tw = (const cpx<T>*)pp.ax.tw;
-        for (int i = threadIdx.x; i < N; i += FAST_THREADS) {
-            tws[i] = ldg(tw + i);
-            ksqs[i] = pp.tabs.ksq[AXIS][i];
-            dks[i] = pp.tabs.dk[AXIS][i];
-        }
+    static_assert(TwTable<N>::SIZE <= N, "per-stage twiddle tables fit N entries");
+    fill_stage_twiddles<T, N>(tws, (const cpx<T>*)pp.ax.tw);
+    for (int i = threadIdx.x; i < N; i += FAST_THREADS) {
+        ksqs[i] = pp.tabs.ksq[AXIS][i];
+        dks[i] = pp.tabs.dk[AXIS][i];
     }
     const int n0 = pp.n0, n1 = pp.n1, n2h = pp.n2h;
     const int nitems = ntiles * pp.njobs;

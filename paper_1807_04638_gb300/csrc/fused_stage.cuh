@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
 
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
-    for (int i = threadIdx.x; i < N; i += FAST_THREADS) tws[i] = ldg(a.tw + i);
+    static_assert(TwTable<N>::SIZE <= N, "per-stage twiddle tables fit N entries");
+    fill_stage_twiddles<float, N>(tws, a.tw);
     for (int i = threadIdx.x; i < NH; i += FAST_THREADS) dks[i] = __ldg(a.dk2 + i);
     // the (tile, line) units of this block in order; the first NBUF - 1 go in
     // flight now, and each line sends the one NBUF - 1 ahead
