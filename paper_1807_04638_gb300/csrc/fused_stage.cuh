@@ -499,20 +499,31 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                 for (int m = 0; m < E; ++m) x[m] = mk(Rq[TPL * m], Rq[RP + TPL * m]);
             }
             fast_fft<float, N, 1, true>(x, b0, b1, c, t, tws, -1);
-            // stage the packed spectrum to pair Z_k with Z_{N-k}
+            // every warp is done with the previous line's outputs in H
             __syncthreads();
-#pragma unroll
-            for (int m = 0; m < E; ++m) b0[SIdx<float, N, 1>::at(c, t + TPL * m)] = x[m];
-            __syncthreads();
+            // unpack the two real rows' spectra: Z_k is register m of lane t
+            // (k = t + TPL m); Z_{N-k} is register E - 1 - m of lane TPL - t
+            // of the same line, or register (E - m) mod E of lane 0 itself
             // tangent: H[0][row] and H[1][row] are the two fields of the row;
             // adjoint: H[q][row] is field q of the line
-            const int ha = KIND == 0 ? c : q * TL + 2 * rp;
-            const int hb = KIND == 0 ? TL + c : q * TL + 2 * rp + 1;
-            for (int k = t; k < nb2; k += TPL) {
-                const cpx<float> zk = b0[SIdx<float, N, 1>::at(c, k)];
-                const cpx<float> zn = cj(b0[SIdx<float, N, 1>::at(c, k == 0 ? 0 : N - k)]);
-                H[ha * PH + k] = 0.5f * (zk + zn);
-                H[hb * PH + k] = rot(0.5f * (zk - zn), -1);
+            {
+                const int ha = KIND == 0 ? c : q * TL + 2 * rp;
+                const int hb = KIND == 0 ? TL + c : q * TL + 2 * rp + 1;
+                const int lane = threadIdx.x & 31;
+                const int src = (lane & ~(TPL - 1)) | ((TPL - t) & (TPL - 1));
+#pragma unroll
+                for (int m = 0; m <= E / 2; ++m) {
+                    if (TPL * m >= nb2) break;  // the same for every lane
+                    const float px = __shfl_sync(0xffffffffu, x[E - 1 - m].x, src);
+                    const float py = __shfl_sync(0xffffffffu, x[E - 1 - m].y, src);
+                    const int k = t + TPL * m;
+                    const cpx<float> zk = x[m];
+                    const cpx<float> zn = cj(t == 0 ? x[(E - m) % E] : mk(px, py));
+                    if (k < nb2) {
+                        H[ha * PH + k] = 0.5f * (zk + zn);
+                        H[hb * PH + k] = rot(0.5f * (zk - zn), -1);
+                    }
+                }
             }
             __syncthreads();
             // outputs of this line: one combined F(s) + i kappa_2 F(f_2), or two plain
