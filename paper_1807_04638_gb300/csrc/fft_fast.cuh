@@ -214,6 +214,20 @@ __device__ __forceinline__ void fast_fft(cpx<T> (&x)[FastPlan<N>::E], cpx<T>* b0
     fast_stages<T, N, E, N / E, FastPlan<N>::RADS, 0, 1, MAP, TWS>(x, b0, b1, c, t, tw, dir);
 }
 
+// conj(Z_{N-k}) for element k = t + TPL m of a line transform held as the
+// register-blocked passes leave it (element t + TPL m in register m of lane
+// t of the line's TPL consecutive lanes): register E - 1 - m of lane TPL - t,
+// or register (E - m) mod E of lane 0 itself.  Every lane of the warp must
+// call it (warp shuffles); m must be a compile-time index after unrolling.
+template <class T, int E, int TPL>
+__device__ __forceinline__ cpx<T> partner_conj(const cpx<T> (&x)[E], int t, int m) {
+    const int lane = threadIdx.x & 31;
+    const int src = (lane & ~(TPL - 1)) | ((TPL - t) & (TPL - 1));
+    const T px = __shfl_sync(0xffffffffu, x[E - 1 - m].x, src);
+    const T py = __shfl_sync(0xffffffffu, x[E - 1 - m].y, src);
+    return t == 0 ? cj(x[(E - m) % E]) : mk(px, -py);
+}
+
 // ---------------------------------------------------------------- async copies
 // 16-byte asynchronous global -> shared copies (cp.async, completion by
 // commit / wait groups: no polling loop).
@@ -576,15 +590,15 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOcc<T, N>::value)) k_fast_a
                 x[m] = mk(a, b);
             }
             fast_fft<T, N, 1>(x, b0, b1, c, t, tw, -1);
-            // stage the packed spectrum to pair Z_k with Z_{N-k}
-            __syncthreads();
-#pragma unroll
-            for (int m = 0; m < E; ++m) b0[SIdx<T, N, 1>::at(c, t + TPL * m)] = x[m];
-            __syncthreads();
+            // pair Z_k with Z_{N-k} (warp shuffles; the H rows are this line's)
             const SymT<T> sy = job.isym[q];
-            for (int k = t; k < nb2; k += TPL) {
-                const cpx<T> zk = b0[SIdx<T, N, 1>::at(c, k)];
-                const cpx<T> zn = cj(b0[SIdx<T, N, 1>::at(c, k == 0 ? 0 : N - k)]);
+#pragma unroll
+            for (int m = 0; m <= E / 2; ++m) {
+                if (TPL * m >= nb2) break;  // the same for every lane
+                const cpx<T> zn = partner_conj<T, E, TPL>(x, t, m);
+                const cpx<T> zk = x[m];
+                const int k = t + TPL * m;
+                if (k >= nb2) continue;
                 cpx<T> sa, sb;
                 if constexpr (sizeof(T) == 4) {
                     const cpx<T> sc = sym_coef(sy, pp.tabs, 0, 0, k);  // same for both rows
@@ -755,15 +769,15 @@ __global__ void __launch_bounds__(FAST_THREADS, A2P_BLOCKS) k_fast_axis2p(const 
             // every line must have read its rows first
             if constexpr (SIdx<T, N, 1>::LP != N) __syncthreads();
             fast_fft<T, N, 1>(x, b0, b1, c, t, tw, -1);
-            // stage the packed spectrum to pair Z_k with Z_{N-k}
-            __syncthreads();
-#pragma unroll
-            for (int m = 0; m < E; ++m) b0[SIdx<T, N, 1>::at(c, t + TPL * m)] = x[m];
-            __syncthreads();
+            // pair Z_k with Z_{N-k} (warp shuffles; the H rows are this line's)
             const SymT<T> sy = job.isym[q];
-            for (int k = t; k < nb2; k += TPL) {
-                const cpx<T> zk = b0[SIdx<T, N, 1>::at(c, k)];
-                const cpx<T> zn = cj(b0[SIdx<T, N, 1>::at(c, k == 0 ? 0 : N - k)]);
+#pragma unroll
+            for (int m = 0; m <= E / 2; ++m) {
+                if (TPL * m >= nb2) break;  // the same for every lane
+                const cpx<T> zn = partner_conj<T, E, TPL>(x, t, m);
+                const cpx<T> zk = x[m];
+                const int k = t + TPL * m;
+                if (k >= nb2) continue;
                 const cpx<T> sc = sym_coef(sy, pp.tabs, 0, 0, k);
                 const cpx<T> sa = sym_mul(sc, (T)0.5 * (zk + zn));
                 const cpx<T> sbv = sym_mul(sc, rot((T)0.5 * (zk - zn), -1));

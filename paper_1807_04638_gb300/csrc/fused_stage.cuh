@@ -509,16 +509,12 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
             {
                 const int ha = KIND == 0 ? c : q * TL + 2 * rp;
                 const int hb = KIND == 0 ? TL + c : q * TL + 2 * rp + 1;
-                const int lane = threadIdx.x & 31;
-                const int src = (lane & ~(TPL - 1)) | ((TPL - t) & (TPL - 1));
 #pragma unroll
                 for (int m = 0; m <= E / 2; ++m) {
                     if (TPL * m >= nb2) break;  // the same for every lane
-                    const float px = __shfl_sync(0xffffffffu, x[E - 1 - m].x, src);
-                    const float py = __shfl_sync(0xffffffffu, x[E - 1 - m].y, src);
+                    const cpx<float> zn = partner_conj<float, E, TPL>(x, t, m);
                     const int k = t + TPL * m;
                     const cpx<float> zk = x[m];
-                    const cpx<float> zn = cj(t == 0 ? x[(E - m) % E] : mk(px, py));
                     if (k < nb2) {
                         H[ha * PH + k] = 0.5f * (zk + zn);
                         H[hb * PH + k] = rot(0.5f * (zk - zn), -1);
