@@ -782,7 +782,14 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
-        run_native(args, rank, world)
+        import torch
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+        torch.cuda.set_device(dev)
+        # the handles and the tensors around them live on a stream of their
+        # own, as a user's would: the legacy default stream cannot be captured,
+        # so the Hessian-vector product's CUDA graph needs another stream
+        with torch.cuda.stream(torch.cuda.Stream(dev)):
+            run_native(args, rank, world)
     if world > 1 and args.impl == "native":
         import torch.distributed as td
         td.destroy_process_group()

@@ -199,6 +199,12 @@ inline bool force_unfused() {
     const char* e = getenv("LDDMM_UNFUSED");
     return e && e[0] == '1';
 }
+// LDDMM_NO_GRAPH=1 launches the Hessian-vector product's kernels one by one
+// instead of replaying its recorded CUDA graph (cross-check).
+inline bool force_no_graph() {
+    const char* e = getenv("LDDMM_NO_GRAPH");
+    return e && e[0] == '1';
+}
 // LDDMM_FULL_BAND=1 transforms every spectral line even where the 2/3-rule
 // band makes most of them zero; used to cross-check the band-limited passes.
 inline bool force_full_band() {
@@ -515,6 +521,7 @@ class Engine : public EngineBase {
     Engine(const Dims& dd, const lddmm_params& p, cudaStream_t s) : d(dd), prm(p), st(s) {}
 
     ~Engine() override {
+        if (hvg.exec) cudaGraphExecDestroy(hvg.exec);
         for (auto& x : ev) cudaEventDestroy(x);
         if (scan_ev) cudaEventDestroy(scan_ev);
         // stream-ordered: the workspace returns to the pool after the
@@ -1684,6 +1691,53 @@ class Engine : public EngineBase {
             spec_to_real2(v0full, sym(w2, 1, -1), adj_result(), sym(1.0, 0, -1, 1), grad);
         lin_valid = true;
     }
+    // ---- the Hessian-vector product as a CUDA graph.  Its ~220 launches
+    // depend only on the handle and on (dv0, out, space): they are recorded
+    // once (stream capture) and replayed, which removes the gaps between
+    // back-to-back launches.  Not with the profiler on (it times each
+    // launch), with checkpointed states (the re-shooting depends on which
+    // segment is resident), or when the stream cannot be captured (the
+    // legacy default stream): then the kernels are launched one by one.
+    struct HvGraph {
+        const void* in = nullptr;
+        void* out = nullptr;
+        int space = -1;
+        cudaGraphExec_t exec = nullptr;
+    };
+    HvGraph hvg;
+    void hessvec_run(const T* dv0, T* out, int space) {
+        if (prof_on || ckpt || force_no_graph()) {
+            hessvec_core(dv0, out, space);
+            return;
+        }
+        if (!(hvg.exec && hvg.in == dv0 && hvg.out == out && hvg.space == space)) {
+            if (hvg.exec) {
+                cudaGraphExecDestroy(hvg.exec);
+                hvg.exec = nullptr;
+            }
+            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                cudaGetLastError();
+                hessvec_core(dv0, out, space);
+                return;
+            }
+            hessvec_core(dv0, out, space);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (e != cudaSuccess || !g || cudaGraphInstantiate(&hvg.exec, g, 0) != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                hvg.exec = nullptr;
+                cudaGetLastError();
+                hessvec_core(dv0, out, space);  // the captured launches did not run
+                return;
+            }
+            cudaGraphDestroy(g);
+            hvg.in = dv0;
+            hvg.out = out;
+            hvg.space = space;
+        }
+        if (cudaGraphLaunch(hvg.exec, st) != cudaSuccess) fail(LDDMM_ERR_CUDA);
+    }
+
     void hessvec_core(const T* dv0, T* out, int space) {
         NvtxRange nr_("lddmm hessvec");
         fwd_vec(dv0, dhat);
@@ -1751,7 +1805,7 @@ class Engine : public EngineBase {
         if (!dv0 || !Hdv) return fail(LDDMM_ERR_ARG);
         if (!lin_valid) return LDDMM_ERR_NOT_LINEARIZED;
         scan_inputs({{dv0, 3 * d.N}});
-        hessvec_core((const T*)dv0, (T*)Hdv, prm.space);
+        hessvec_run((const T*)dv0, (T*)Hdv, prm.space);
         return finish();
     }
 
@@ -1975,7 +2029,7 @@ class Engine : public EngineBase {
             const double nrm0 = prm.space == LDDMM_SPACE_V ? std::sqrt(std::max(rz, 0.0)) : std::sqrt(dot_now(pr, pr, n3));
             int pit = 0;
             while (pit < prm.pcg_maxit) {
-                hessvec_core(pp, pq, LDDMM_SPACE_L2);
+                hessvec_run(pp, pq, LDDMM_SPACE_L2);
                 const double pq_ = dot_now(pp, pq, n3);
                 if (!(pq_ > 0.0)) break;
                 const double alpha = rz / pq_;
