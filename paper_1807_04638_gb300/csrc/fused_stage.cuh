@@ -38,12 +38,13 @@
 //   2 (ad_v^T):  out[9c + 3g] = F2(s) + i kappa_2 F2(f_2),
 //                out[9c + 3g + 1] = F2(f_0), out[9c + 3g + 2] = F2(f_1);
 //   optional real cotangents eta_src (3 fields) are added to s of group 0.
-//   Its line transforms pack two rows of one field, as the separate axis-2
-//   pass does (fields of one row can differ widely in size, and a transform
-//   that packed two of them would leave the rounding of the larger in the
-//   smaller, which the derivative symbols then amplify): each field is handed
-//   between the row's owner and the row pair's line group through shared
-//   memory.
+//   Its inverse lines and its (s, f_2) forward lines pack two rows of one
+//   field, as the separate axis-2 pass does (fields of one row can differ
+//   widely in size, and a transform that packed s with f_2 would leave the
+//   rounding of the larger in the smaller, which i kappa_2 then amplifies):
+//   those fields are handed between the row's owner and the row pair's line
+//   group through shared memory.  Its (f_0, f_1) forward lines, fields of
+//   one group alike in size, pack the two fields of the owner's row.
 #pragma once
 #include "fft_fast.cuh"
 #include "pw_kernels.cuh"
@@ -484,19 +485,23 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                     default: break;
                 }
                 if (f + 1 < NLO) prefetch_line_fields<SS, N, TL>(tile_states, a.npts, (f + 1) / 6, (f + 1) % 6);
-                // the two fields of this row go to the line groups that
-                // transform them on row pairs (two rows of one field share a
-                // transform, as in the separate axis-2 pass)
-                float* const Ro = R + c * RP + t;
+                if (f % 2 == 0) {
+                    // (s, f_2): the two fields go to the line groups that
+                    // transform them on row pairs (two rows of one field share
+                    // a transform, as in the separate axis-2 pass); (f_0, f_1)
+                    // of one group are alike in size and share this row's
+                    // transform
+                    float* const Ro = R + c * RP + t;
 #pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    Ro[TPL * m] = x[m].x;
-                    Ro[FS + TPL * m] = x[m].y;
+                    for (int m = 0; m < E; ++m) {
+                        Ro[TPL * m] = x[m].x;
+                        Ro[FS + TPL * m] = x[m].y;
+                    }
+                    __syncthreads();
+                    const float* const Rq = R + q * FS + 2 * rp * RP + t;
+#pragma unroll
+                    for (int m = 0; m < E; ++m) x[m] = mk(Rq[TPL * m], Rq[RP + TPL * m]);
                 }
-                __syncthreads();
-                const float* const Rq = R + q * FS + 2 * rp * RP + t;
-#pragma unroll
-                for (int m = 0; m < E; ++m) x[m] = mk(Rq[TPL * m], Rq[RP + TPL * m]);
             }
             fast_fft<float, N, 1, true>(x, b0, b1, c, t, tws, -1);
             // every warp is done with the previous line's outputs in H
@@ -504,11 +509,13 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
             // unpack the two real rows' spectra: Z_k is register m of lane t
             // (k = t + TPL m); Z_{N-k} is register E - 1 - m of lane TPL - t
             // of the same line, or register (E - m) mod E of lane 0 itself
-            // tangent: H[0][row] and H[1][row] are the two fields of the row;
-            // adjoint: H[q][row] is field q of the line
+            // field-pair lines (tangent, adjoint (f_0, f_1)): H[0][row] and
+            // H[1][row] are the two fields of the row; row-pair lines
+            // (adjoint (s, f_2)): H[q][row] is field q of the line
             {
-                const int ha = KIND == 0 ? c : q * TL + 2 * rp;
-                const int hb = KIND == 0 ? TL + c : q * TL + 2 * rp + 1;
+                const bool rowpair = KIND == 1 && f % 2 == 0;
+                const int ha = rowpair ? q * TL + 2 * rp : c;
+                const int hb = rowpair ? q * TL + 2 * rp + 1 : TL + c;
 #pragma unroll
                 for (int m = 0; m <= E / 2; ++m) {
                     if (TPL * m >= nb2) break;  // the same for every lane
