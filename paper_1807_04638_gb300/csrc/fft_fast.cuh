@@ -463,6 +463,16 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
             }
         } else {
             // forward: FFT of each input, post-symbol, accumulate; bases and store after the last
+            if (last && valid) {
+                // the bases are read after the transform: bring them into L1 now
+                const int g0t = gidx(t);
+                const int sm = AXIS == 1 ? TPL : TPL * n1;
+                for (int b = 0; b < job.nb; ++b) {
+                    const cpx<T>* bp = (const cpx<T>*)job.base[b] + g0t;
+#pragma unroll
+                    for (int m = 0; m < E; ++m) asm volatile("prefetch.global.L1 [%0];" ::"l"(bp + m * sm));
+                }
+            }
 #pragma unroll
             for (int m = 0; m < E; ++m) x[m] = valid ? tile[at(t + TPL * m)] : mk((T)0, (T)0);
             __syncthreads();
