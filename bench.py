@@ -147,19 +147,21 @@ def workload_inputs(n=N128, seed=1):
     return P, v0, e0, e1, d
 
 
-# DRAM traffic per launch of the dominant kernel class, from an ncu capture
-# (profiles/hv_128cubed_f32_launch_list.md), valid only for the kernel sources
-# it was measured on: reported as null once the sources change.
-TRAFFIC = {"digest": "51ad7e7bc4fa3671", "fft_axis2_r2c_c2r": 136.1e6}
+# DRAM traffic per launch of the stage kernels, from an ncu capture
+# (profiles/fused_stages_128cubed_f32_ncu.md; one launch is one stage over the
+# whole grid, the same at every nt), valid only for the kernel sources it was
+# measured on: reported as null once the sources change.
+TRAFFIC = {"digest": "81ab0fb1523c98c2", "adjoint_stage_fused": 360.1e6, "tangent_stage_fused": 384.5e6}
 
 
 def kernel_digest():
-    """Digest of the FFT pass sources (the dominant kernel class and its job
-    layout): a stored DRAM-traffic figure holds only for this digest."""
+    """Digest of the pass and stage-kernel sources (the dominant kernel
+    classes and their job layout): a stored DRAM-traffic figure holds only
+    for this digest."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1807_04638_gb300", "csrc")
-    for f in ("common.cuh", "fft_fast.cuh", "fft_kernels.cuh"):
+    for f in ("common.cuh", "fft_fast.cuh", "fft_kernels.cuh", "fused_stage.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
