@@ -240,44 +240,91 @@ template <int P> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(P) : "memory");
 }
 
-// sym_apply for an element of a line along axis AX whose index on that axis
-// is p: the line axis' kappa^2 and derivative tables are read from shared
-// memory (ksqs, dks), the fixed axes' entries from the global tables (the
-// same for every element of the line).  Same arithmetic as sym_apply.
-template <class T, int AX>
-__device__ __forceinline__ cpx<T> sym_apply_line(const SymT<T>& sy, const SpecTabs<T>& tb, const T* ksqs,
-                                                 const T* dks, int k0, int k1, int k2, cpx<T> v) {
+// sym_apply over the E elements a thread holds of a line along axis AX
+// (element m has index p = t + TPL m on that axis), in place.  The branches
+// on the symbol's fields and the fixed axes' table entries are taken once per
+// line, not per element; the line axis' kappa^2 and derivative tables are
+// read from shared memory (ksqs, dks).  Every element gets sym_apply's
+// arithmetic in sym_apply's order.
+// kf0, kf1: the indices of the two fixed axes (k0 or k1, then k2).
+template <class T, int AX, int E, int TPL>
+__device__ __forceinline__ void sym_line(const SymT<T>& sy, const SpecTabs<T>& tb, const T* ksqs, const T* dks,
+                                         int kf0, int k2, int t, cpx<T> (&v)[E]) {
+    constexpr int AO = AX == 0 ? 1 : 0;  // the other in-plane axis (fixed along the line)
     if (sy.mask) {
-        const bool out0 = k0 > tb.kcut[0] && k0 < tb.n[0] - tb.kcut[0];
-        const bool out1 = k1 > tb.kcut[1] && k1 < tb.n[1] - tb.kcut[1];
-        if (out0 || out1 || k2 > tb.kcut[2]) return mk((T)0, (T)0);
-    }
-    T f = sy.scale;
-    if (sy.lpow != 0) {
-        const T q0 = AX == 0 ? ksqs[k0] : tb.ksq[0][k0];
-        const T q1 = AX == 1 ? ksqs[k1] : tb.ksq[1][k1];
-        const T base = (T)1 + tb.alpha * (q0 + q1 + tb.ksq[2][k2]);
-        const int e = tb.s * (sy.lpow > 0 ? sy.lpow : -sy.lpow);
-        T pw;
-        if (e == 2) {
-            pw = base * base;
-        } else if (e == 4) {
-            pw = base * base;
-            pw = pw * pw;
-        } else {
-            pw = (T)1;
-            for (int q = 0; q < e; ++q) pw *= base;
+        // fixed axes outside the band: the whole line is zero
+        const bool outl = (kf0 > tb.kcut[AO] && kf0 < tb.n[AO] - tb.kcut[AO]) || k2 > tb.kcut[2];
+        if (outl) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = mk((T)0, (T)0);
+            return;
         }
-        f = sy.lpow > 0 ? f * pw : sym_div(f, pw);
+    }
+    T f[E];
+    if (sy.lpow != 0) {
+        const T qo = tb.ksq[AO][kf0], q2 = tb.ksq[2][k2];
+        T base[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const T qa = ksqs[t + TPL * m];
+            base[m] = (T)1 + tb.alpha * ((AX == 0 ? qa + qo : qo + qa) + q2);
+        }
+        const int e = tb.s * (sy.lpow > 0 ? sy.lpow : -sy.lpow);
+        if (e == 2) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) base[m] = base[m] * base[m];
+        } else if (e == 4) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const T b2 = base[m] * base[m];
+                base[m] = b2 * b2;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                T pw = (T)1;
+                for (int q = 0; q < e; ++q) pw *= base[m];
+                base[m] = pw;
+            }
+        }
+        if (sy.lpow > 0) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) f[m] = sy.scale * base[m];
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) f[m] = sym_div(sy.scale, base[m]);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) f[m] = sy.scale;
     }
     if (sy.deriv >= 0) {
-        T dk;
-        if (sy.deriv == AX) dk = dks[AX == 0 ? k0 : k1];
-        else dk = tb.dk[sy.deriv][sy.deriv == 0 ? k0 : (sy.deriv == 1 ? k1 : k2)];
-        const T d = dk * f;
-        return mk(-d * v.y, d * v.x);
+        if (sy.deriv == AX) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const T d = dks[t + TPL * m] * f[m];
+                v[m] = mk(-d * v[m].y, d * v[m].x);
+            }
+        } else {
+            const T dk = tb.dk[sy.deriv][sy.deriv == 2 ? k2 : kf0];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const T d = dk * f[m];
+                v[m] = mk(-d * v[m].y, d * v[m].x);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = mk(f[m] * v[m].x, f[m] * v[m].y);
     }
-    return mk(f * v.x, f * v.y);
+    if (sy.mask) {
+        // line-axis entries outside the band
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int p = t + TPL * m;
+            if (p > tb.kcut[AX] && p < tb.n[AX] - tb.kcut[AX]) v[m] = mk((T)0, (T)0);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- C2C passes
@@ -447,11 +494,8 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
                 for (int o = 0; o < job.nout; ++o) {
                     const SymT<T> sy = job.osym[o];
 #pragma unroll
-                    for (int m = 0; m < E; ++m) {
-                        const int p = t + TPL * m;
-                        x[m] = sym_apply_line<T, AXIS>(sy, pp.tabs, ksqs, dks, AXIS == 0 ? p : k0b,
-                                                       AXIS == 1 ? p : k1b, k2b, acc[m]);
-                    }
+                    for (int m = 0; m < E; ++m) x[m] = acc[m];
+                    sym_line<T, AXIS, E, TPL>(sy, pp.tabs, ksqs, dks, AXIS == 0 ? k1b : k0b, k2b, t, x);
                     fast_fft<T, N, MAP, true>(x, b0, b1, c, t, tws, +1);
                     if (valid) {
                         cpx<T>* ob = (cpx<T>*)job.out[o] + gidx(t);
@@ -478,13 +522,9 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
             __syncthreads();
             fast_fft<T, N, MAP, true>(x, b0, b1, c, t, tws, -1);
             const SymT<T> sy = job.isym[q];
+sym_line<T, AXIS, E, TPL>(sy, pp.tabs, ksqs, dks, AXIS == 0 ? k1b : k0b, k2b, t, x);
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int p = t + TPL * m;
-                const cpx<T> v = sym_apply_line<T, AXIS>(sy, pp.tabs, ksqs, dks, AXIS == 0 ? p : k0b,
-                                                         AXIS == 1 ? p : k1b, k2b, x[m]);
-                acc[m] = q == 0 ? v : acc[m] + v;
-            }
+            for (int m = 0; m < E; ++m) acc[m] = q == 0 ? x[m] : acc[m] + x[m];
             if (last && valid) {
                 const int g0t = gidx(t);
                 const int sm = AXIS == 1 ? TPL : TPL * n1;  // element step between m
