@@ -262,6 +262,44 @@ __device__ __forceinline__ void adj_fields(cpx<float> (&x)[E], const float (&acc
     }
 }
 
+// Element m of thread t of a line (k = t + TPL m) in a C2R line transform
+// that packs two real rows (u, v) as u + i v: the half-spectrum index kk it
+// reads (k, or N - k with conjugation above N / 2) and whether the entry is
+// one of the real ones (k = 0, N / 2).  With E = 8 the element's range is
+// known from m: m < 4 below N / 2, m = 4 at N / 2 + t, m > 4 above.
+template <int N, int TPL> struct HermIdx {
+    int kk;
+    bool conj, real;
+    __device__ __forceinline__ HermIdx(int t, int m) {
+        static_assert(N == 8 * TPL, "E = 8 plans");
+        if (m < 4) {
+            kk = t + TPL * m;
+            conj = false;
+            real = m == 0 && t == 0;
+        } else if (m == 4) {
+            kk = N / 2 - t;
+            conj = t != 0;
+            real = t == 0;
+        } else {
+            kk = N - TPL * m - t;
+            conj = true;
+            real = false;
+        }
+    }
+    // the line's entry u + i v, u and v the rows' half-spectrum values at kk
+    __device__ __forceinline__ cpx<float> pack(cpx<float> u, cpx<float> v) const {
+        if (real) {
+            u.y = 0.f;
+            v.y = 0.f;
+        }
+        if (conj) {
+            u = cj(u);
+            v = cj(v);
+        }
+        return mk(u.x - v.y, u.y + v.x);
+    }
+};
+
 // inputs of inverse line l: (i0, i1); i1 = -1: the line packs (in[i0],
 // D2 in[i0]) (tangent only)
 template <int KIND> __device__ __forceinline__ void fused_line_inputs(int l, int& i0, int& i1) {
@@ -372,55 +410,42 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                 int i0, i1;
                 fused_line_inputs<KIND>(l, i0, i1);
                 const cpx<float>* SA = stg + c;
-                const cpx<float>* SB = SA + nb2 * SP;
+                if (i1 < 0) {
 #pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    const int k = t + TPL * m;
-                    const bool lo = k < NH;
-                    const int kk = lo ? k : N - k;
-                    cpx<float> u = mk(0.f, 0.f), v = mk(0.f, 0.f);
-                    if (kk < nb2) {
-                        u = SA[kk * SP];
-                        if (i1 < 0) {
-                            const float d = dks[kk];
+                    for (int m = 0; m < E; ++m) {
+                        const HermIdx<N, TPL> h(t, m);
+                        cpx<float> u = mk(0.f, 0.f), v = mk(0.f, 0.f);
+                        if (h.kk < nb2) {
+                            u = SA[h.kk * SP];
+                            const float d = dks[h.kk];
                             v = mk(-d * u.y, d * u.x);
-                        } else {
-                            v = SB[kk * SP];
                         }
+                        x[m] = h.pack(u, v);
                     }
-                    if (kk == 0 || kk == N / 2) {
-                        u.y = 0.f;
-                        v.y = 0.f;
+                } else {
+                    const cpx<float>* SB = SA + nb2 * SP;
+#pragma unroll
+                    for (int m = 0; m < E; ++m) {
+                        const HermIdx<N, TPL> h(t, m);
+                        cpx<float> u = mk(0.f, 0.f), v = mk(0.f, 0.f);
+                        if (h.kk < nb2) {
+                            u = SA[h.kk * SP];
+                            v = SB[h.kk * SP];
+                        }
+                        x[m] = h.pack(u, v);
                     }
-                    if (!lo) {
-                        u = cj(u);
-                        v = cj(v);
-                    }
-                    x[m] = mk(u.x - v.y, u.y + v.x);
                 }
             } else {
                 if (l == NLI - 1) prefetch_line_fields<SS, N, TL>(tile_states, a.npts, 0, 0);
                 // one field (input q of the line) on a pair of rows
-                const cpx<float>* SA = stg + q * nb2 * SP + 2 * rp;
+                // the row pair's two entries are adjacent: one 16-byte load
+                const float4* SA = (const float4*)(stg + q * nb2 * SP + 2 * rp);
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
-                    const int k = t + TPL * m;
-                    const bool lo = k < NH;
-                    const int kk = lo ? k : N - k;
-                    cpx<float> u = mk(0.f, 0.f), v = mk(0.f, 0.f);
-                    if (kk < nb2) {
-                        u = SA[kk * SP];
-                        v = SA[kk * SP + 1];
-                    }
-                    if (kk == 0 || kk == N / 2) {
-                        u.y = 0.f;
-                        v.y = 0.f;
-                    }
-                    if (!lo) {
-                        u = cj(u);
-                        v = cj(v);
-                    }
-                    x[m] = mk(u.x - v.y, u.y + v.x);
+                    const HermIdx<N, TPL> h(t, m);
+                    float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (h.kk < nb2) uv = SA[h.kk * (SP / 2)];
+                    x[m] = h.pack(mk(uv.x, uv.y), mk(uv.z, uv.w));
                 }
             }
             fast_fft<float, N, 1, true>(x, b0, b1, c, t, tws, +1);
@@ -534,19 +559,24 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
             int ob;
             if constexpr (KIND == 0) ob = 2 * f;
             else ob = 9 * (f / 6) + 3 * ((f % 6) / 2) + (combined ? 0 : 1);
+            // thread -> (row, first plane): the TL rows of a plane are one
+            // coalesced segment of the [k2][row] layout
+            static_assert(FAST_THREADS % TL == 0, "whole planes per block sweep");
+            const int orow = threadIdx.x % TL;
+            constexpr int KSTEP = FAST_THREADS / TL;
             if (combined) {
-                for (int i = threadIdx.x; i < nb2 * TL; i += FAST_THREADS) {
-                    const int k = i / TL, row = i % TL;
+                cpx<float>* const o = a.out[ob] + r0 + orow;
+                for (int k = threadIdx.x / TL; k < nb2; k += KSTEP) {
                     const float d = dks[k];
-                    const cpx<float> fs = H[row * PH + k], f2 = H[(TL + row) * PH + k];
-                    a.out[ob][(size_t)k * rows + r0 + row] = fs + mk(-d * f2.y, d * f2.x);
+                    const cpx<float> fs = H[orow * PH + k], f2 = H[(TL + orow) * PH + k];
+                    o[(size_t)k * rows] = fs + mk(-d * f2.y, d * f2.x);
                 }
             } else {
-                for (int i = threadIdx.x; i < 2 * nb2 * TL; i += FAST_THREADS) {
-                    const int qq = i / (nb2 * TL);
-                    const int rem = i - qq * nb2 * TL;
-                    const int k = rem / TL, row = rem % TL;
-                    a.out[ob + qq][(size_t)k * rows + r0 + row] = H[(qq * TL + row) * PH + k];
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq) {
+                    cpx<float>* const o = a.out[ob + qq] + r0 + orow;
+                    for (int k = threadIdx.x / TL; k < nb2; k += KSTEP)
+                        o[(size_t)k * rows] = H[(qq * TL + orow) * PH + k];
                 }
             }
         }
