@@ -347,9 +347,11 @@ template <class T> struct FastPass {
 struct FusedPass {
     static bool has(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
     static int tile_rows(int n) { return FAST_THREADS / (n / 8); }
+    static int band_planes(int n) { return (n - 1) / 3 + 1; }  // FusedGeom<n>::NB2
     template <int N, class SS, int KIND> static bool go(const FusedArgs& a, cudaStream_t st, bool set_attr) {
-        if (set_attr) return raise_smem_limit(k_fused_stage<SS, N, KIND>, FusedGeom<N>::smem(KIND, N / 2 + 1));
-        const size_t sm = FusedGeom<N>::smem(KIND, a.nb2);
+        if (set_attr) return raise_smem_limit(k_fused_stage<SS, N, KIND>, FusedGeom<N>::smem(KIND));
+        if (a.nb2 != FusedGeom<N>::NB2) return false;
+        const size_t sm = FusedGeom<N>::smem(KIND);
         k_fused_stage<SS, N, KIND><<<persistent_grid(a.ntiles, FUSED_BLOCKS), FAST_THREADS, sm, st>>>(a);
         return true;
     }
@@ -687,7 +689,7 @@ class Engine : public EngineBase {
         band_ok = prm.dealias && fast[0] && fast[1] && fast[2] && !force_full_band() &&
                   (bnb2 < d.n2h || bc1 < bs1);
         if constexpr (sizeof(T) == 4)
-            fused = band_ok && !force_unfused() && FusedPass::has(d.n2) &&
+            fused = band_ok && !force_unfused() && FusedPass::has(d.n2) && bnb2 == FusedPass::band_planes(d.n2) &&
                     d.rows % (size_t)FusedPass::tile_rows(d.n2) == 0 && FusedPass::prepare(d.n2);
         LD_CK(cudaStreamSynchronize(st));
         return LDDMM_OK;
@@ -1439,13 +1441,15 @@ class Engine : public EngineBase {
             const double band = (double)bnb2 * d.rows * sizeof(C);
             const double bytes = 33.0 * band + 24.0 * d.N * state_elem() + (a.eta_src ? 3.0 * d.N * sizeof(T) : 0.0);
             PScope ps_(this, kind == 0 ? KC_TANF : KC_ADJF, bytes);
+            bool ok;
             if (bf16) {
-                if (kind == 0) FusedPass::launch<__nv_bfloat16, 0>(d.n2, a, st);
-                else FusedPass::launch<__nv_bfloat16, 1>(d.n2, a, st);
+                if (kind == 0) ok = FusedPass::launch<__nv_bfloat16, 0>(d.n2, a, st);
+                else ok = FusedPass::launch<__nv_bfloat16, 1>(d.n2, a, st);
             } else {
-                if (kind == 0) FusedPass::launch<float, 0>(d.n2, a, st);
-                else FusedPass::launch<float, 1>(d.n2, a, st);
+                if (kind == 0) ok = FusedPass::launch<float, 0>(d.n2, a, st);
+                else ok = FusedPass::launch<float, 1>(d.n2, a, st);
             }
+            if (!ok) fail(LDDMM_ERR_DEVICE_CHECK);
         }
     }
     // tangent stage: requests per component c (12 c + ...): eta, D_j eta (3),

@@ -18,7 +18,7 @@
 //   a tile is TL consecutive grid rows, one per line group; thread t of a
 //   group owns the points t + TPL*m (m < 8) of its row for the whole tile.
 //   A complex line transform packs two real fields of the same row.
-//   Inputs and outputs are band planes k2 < nb2 in the [k2][row] layout of
+//   Inputs and outputs are band planes k2 < NB2 in the [k2][row] layout of
 //   the axis-2 pass; the next line's inputs are copied (cp.async) into the
 //   other half of a double buffer while the current line is transformed.
 //
@@ -82,16 +82,17 @@ template <int N> struct FusedGeom {
     static constexpr int RP = N + 16;
     static constexpr int FS = TL * RP + 16;
     static constexpr int TWD = N + (NH + 1) / 2;   // twiddles, then kappa_2 (complex slots)
-    // Shared memory: two stage buffers, each the band planes k2 < nb2 of two
+    // band planes of the dealiased grid: |k2| <= (N - 1) / 3 (the 2/3 rule of
+    // the projector P); the stages run only on dealiased grids
+    static constexpr int NB2 = (N - 1) / 3 + 1;
+    // Shared memory: two stage buffers, each the band planes k2 < NB2 of two
     // inputs and at least HS (the forward lines' unpacked outputs H live in
     // the buffer that no copy targets then), two exchange tiles, the tables,
-    // and for the adjoint the hand-off rows.  Sized at launch from nb2: what
+    // and for the adjoint the hand-off rows.  Sized from NB2: what
     // it leaves of the SM's 256 KB serves as L1 for the prefetched states.
-    static __host__ __device__ constexpr int stage_elems(int nb2) {
-        return 2 * nb2 * SP > HS ? 2 * nb2 * SP : HS;
-    }
-    static constexpr size_t smem(int kind, int nb2) {
-        return (size_t)(2 * stage_elems(nb2) + 2 * XT + TWD) * sizeof(cpx<float>) +
+    static constexpr int STG = 2 * NB2 * SP > HS ? 2 * NB2 * SP : HS;
+    static constexpr size_t smem(int kind) {
+        return (size_t)(2 * STG + 2 * XT + TWD) * sizeof(cpx<float>) +
                (kind == 1 ? (size_t)2 * FS * sizeof(float) : 0);
     }
     static_assert(TL % 2 == 0, "the adjoint pairs the rows of a tile");
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
     constexpr int NLO = KIND == 0 ? 3 : 18;   // forward lines per row / rounds
     constexpr int NBUF = 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int STG = G::stage_elems(a.nb2);              // one stage buffer (complex)
+    constexpr int STG = G::STG;                         // one stage buffer (complex)
     cpx<float>* const stage0 = (cpx<float>*)smem_raw;  // buffers stage0 + sb * STG, sb < NBUF
     cpx<float>* const b0 = stage0 + NBUF * STG;
     cpx<float>* const b1 = b0 + G::XT;
@@ -337,7 +338,8 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
     const int c = threadIdx.x / TPL, t = threadIdx.x % TPL;
     // adjoint: a line group transforms one field (q) on a pair of rows (2 rp, 2 rp + 1)
     const int q = c & 1, rp = c >> 1;
-    const int rows = a.rows, nb2 = a.nb2, ntiles = a.ntiles;
+    constexpr int nb2 = G::NB2;
+    const int rows = a.rows, ntiles = a.ntiles;
 
     auto issue = [&](int tile, int l, int buf) {
         if (tile < ntiles) {
