@@ -164,15 +164,50 @@ __device__ __forceinline__ void fill_stage_twiddles(cpx<T>* tws, const cpx<T>* t
     }
 }
 
+// Exchange addressing by XOR (XA).  With the XOR layout (SIdx KIND 2) and N
+// a power of two, the element index of every exchange access splits into a
+// thread part and a compile-time part with disjoint bits (radix digits of t,
+// and of b, r or m), and the layout is linear over XOR: swz(P_t | P_c) =
+// swz(P_t) ^ swz(P_c).  For a line whose shared-memory base is aligned to
+// the line's size (8 N bytes) the byte address is therefore
+// (base | 8 swz(P_t)) ^ 8 swz(P_c): one per-thread value per exchange, and
+// one XOR with a constant per access.  The caller guarantees the alignment.
+template <class T, int N> struct XorEx {
+    static constexpr bool ok = sizeof(T) == 4 && SIdx<T, N, 1>::KIND == 2 && (N & (N - 1)) == 0;
+    static __host__ __device__ constexpr int lg(int v) { return v <= 1 ? 0 : 1 + lg(v / 2); }
+};
+__device__ __forceinline__ void sts_v2(unsigned a, cpx<float> v) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ cpx<float> lds_v2(unsigned a) {
+    cpx<float> v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+
+// p advanced to the next ALIGN-byte boundary of the shared window (the
+// kernel allocates ALIGN - 16 bytes more than it uses)
+template <int ALIGN> __device__ __forceinline__ unsigned char* align_smem(unsigned char* p) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+    return p + ((ALIGN - (s & (ALIGN - 1))) & (ALIGN - 1));
+}
+
 // TWS: the twiddles are the per-stage tables in shared memory (else the
-// global table, read through the read-only cache)
-template <class T, int N, int E, int TPL, int RADS, int S, int NS, int MAP, bool TWS = false>
+// global table, read through the read-only cache); XA: exchange addressing
+// by XOR (MAP 1 lines of an XorEx<T, N>::ok plan on 8N-byte aligned tiles)
+template <class T, int N, int E, int TPL, int RADS, int S, int NS, int MAP, bool TWS = false, bool XA = false>
 __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* b1, int c, int t, const cpx<T>* tw,
                                             int dir) {
     constexpr int R = (RADS >> (4 * S)) & 0xF;
     constexpr bool LAST = NS * R == N;
     constexpr int B = E / R;
     static_assert(B * R == E, "radix must divide the per-thread element count");
+    static_assert(!XA || (MAP == 1 && XorEx<T, N>::ok), "XOR addressing needs the XOR layout of a power-of-two line");
+    using SI = SIdx<T, N, MAP>;
+    constexpr unsigned CB = (unsigned)sizeof(cpx<T>);
+    // XA: this line's base in the shared window
+    unsigned lb = 0;
+    if constexpr (XA) lb = (unsigned)__cvta_generic_to_shared(b0) + (unsigned)(c * SI::LP) * CB;
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int j = t + TPL * b;
@@ -192,26 +227,44 @@ __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* 
         if constexpr (LAST) {
 #pragma unroll
             for (int r = 0; r < R; ++r) x[b + B * r] = v[r];
+        } else if constexpr (XA) {
+            // store index (j / NS) NS R + k + r NS: thread part from t, the
+            // rest from b and r
+            constexpr int LNS = XorEx<T, N>::lg(NS), LR = XorEx<T, N>::lg(R);
+            const int pt = ((t >> LNS) << (LNS + LR)) | (t & (NS - 1));
+            const unsigned as = lb | CB * (unsigned)SI::swz(pt);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int pc = (((TPL * b) >> LNS) << (LNS + LR)) | ((TPL * b) & (NS - 1)) | (r << LNS);
+                sts_v2(as ^ CB * (unsigned)SI::swz(pc), v[r]);
+            }
         } else {
             const int base = (j / NS) * NS * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) b0[SIdx<T, N, MAP>::at(c, base + r * NS)] = v[r];
+            for (int r = 0; r < R; ++r) b0[SI::at(c, base + r * NS)] = v[r];
         }
     }
     if constexpr (!LAST) {
         line_sync<MAP, TPL>();
+        if constexpr (XA) {
+            // load index t + TPL m
+            const unsigned al = lb | CB * (unsigned)SI::swz(t);
 #pragma unroll
-        for (int m = 0; m < E; ++m) x[m] = b0[SIdx<T, N, MAP>::at(c, t + TPL * m)];
-        fast_stages<T, N, E, TPL, RADS, S + 1, NS * R, MAP, TWS>(x, b1, b0, c, t, tw, dir);
+            for (int m = 0; m < E; ++m) x[m] = lds_v2(al ^ CB * (unsigned)SI::swz(TPL * m));
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) x[m] = b0[SI::at(c, t + TPL * m)];
+        }
+        fast_stages<T, N, E, TPL, RADS, S + 1, NS * R, MAP, TWS, XA>(x, b1, b0, c, t, tw, dir);
     }
 }
 
-template <class T, int N, int MAP, bool TWS = false>
+template <class T, int N, int MAP, bool TWS = false, bool XA = false>
 __device__ __forceinline__ void fast_fft(cpx<T> (&x)[FastPlan<N>::E], cpx<T>* b0, cpx<T>* b1, int c, int t,
                                          const cpx<T>* tw, int dir) {
     constexpr int E = FastPlan<N>::E;
     line_sync<MAP, N / E>();  // the line's tiles may still be read by its previous transform
-    fast_stages<T, N, E, N / E, FastPlan<N>::RADS, 0, 1, MAP, TWS>(x, b0, b1, c, t, tw, dir);
+    fast_stages<T, N, E, N / E, FastPlan<N>::RADS, 0, 1, MAP, TWS, XA>(x, b0, b1, c, t, tw, dir);
 }
 
 // conj(Z_{N-k}) for element k = t + TPL m of a line transform held as the

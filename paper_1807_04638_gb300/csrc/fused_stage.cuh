@@ -90,12 +90,18 @@ template <int N> struct FusedGeom {
     // the buffer that no copy targets then), two exchange tiles, the tables,
     // and for the adjoint the hand-off rows.  Sized from NB2: what
     // it leaves of the SM's 256 KB serves as L1 for the prefetched states.
-    static constexpr int STG = 2 * NB2 * SP > HS ? 2 * NB2 * SP : HS;
+    // exchanges addressed by XOR (XorEx): every tile starts on a line-size
+    // (8 N byte) boundary of the shared window
+    static constexpr bool XA = XorEx<float, N>::ok;
+    static constexpr int XAL = XA ? N * (int)sizeof(cpx<float>) : 16;
+    static constexpr int STG0 = 2 * NB2 * SP > HS ? 2 * NB2 * SP : HS;
+    static constexpr int STG = XA ? (STG0 + N - 1) / N * N : STG0;
     static constexpr size_t smem(int kind) {
-        return (size_t)(2 * STG + 2 * XT + TWD) * sizeof(cpx<float>) +
+        return (size_t)(XAL - 16) + (size_t)(2 * STG + 2 * XT + TWD) * sizeof(cpx<float>) +
                (kind == 1 ? (size_t)2 * FS * sizeof(float) : 0);
     }
     static_assert(TL % 2 == 0, "the adjoint pairs the rows of a tile");
+    static_assert(!XA || (STG % N == 0 && XT % N == 0), "exchange tiles on line-size boundaries");
 };
 
 __device__ __forceinline__ float ldst(const float* p) { return __ldg(p); }
@@ -329,7 +335,8 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
     constexpr int NBUF = 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int STG = G::STG;                         // one stage buffer (complex)
-    cpx<float>* const stage0 = (cpx<float>*)smem_raw;  // buffers stage0 + sb * STG, sb < NBUF
+    constexpr bool XA = G::XA;
+    cpx<float>* const stage0 = (cpx<float>*)align_smem<G::XAL>(smem_raw);  // buffers stage0 + sb * STG, sb < NBUF
     cpx<float>* const b0 = stage0 + NBUF * STG;
     cpx<float>* const b1 = b0 + G::XT;
     cpx<float>* const tws = b1 + G::XT;                 // twiddles
@@ -450,7 +457,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                     x[m] = h.pack(mk(uv.x, uv.y), mk(uv.z, uv.w));
                 }
             }
-            fast_fft<float, N, 1, true>(x, b0, b1, c, t, tws, +1);
+            fast_fft<float, N, 1, true, XA>(x, b0, b1, c, t, tws, +1);
             if constexpr (KIND == 0) {
                 switch (l) {
 #define LDDMM_TC(L) \
@@ -530,7 +537,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                     for (int m = 0; m < E; ++m) x[m] = mk(Rq[TPL * m], Rq[RP + TPL * m]);
                 }
             }
-            fast_fft<float, N, 1, true>(x, b0, b1, c, t, tws, -1);
+            fast_fft<float, N, 1, true, XA>(x, b0, b1, c, t, tws, -1);
             // every warp is done with the previous line's outputs in H
             __syncthreads();
             // unpack the two real rows' spectra: Z_k is register m of lane t
