@@ -251,6 +251,25 @@ inline bool raise_smem_limit(K kernel, size_t need) {
     return false;
 }
 
+// Ask for the smallest shared-memory carveout that holds `blocks` resident
+// blocks of `bytes` dynamic shared memory each, so that the rest of the SM's
+// unified L1/shared storage stays L1 (a hint: the driver rounds it up to a
+// split it supports).
+template <class K>
+inline void prefer_l1(K kernel, size_t bytes, int blocks) {
+    int dev = 0, per_sm = 0, resv = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess || per_sm <= 0) {
+        cudaGetLastError();
+        return;
+    }
+    const size_t need = (size_t)blocks * (bytes + (size_t)resv);
+    const int pct = (int)std::min<size_t>(100, (need * 100 + (size_t)per_sm - 1) / (size_t)per_sm);
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess)
+        cudaGetLastError();  // a hint only
+}
+
 // Grid of a persistent pass: `per_sm` resident blocks per SM, never more
 // blocks than work items.
 inline int persistent_grid(int items, int per_sm = 3) {
@@ -349,7 +368,11 @@ struct FusedPass {
     static int tile_rows(int n) { return FAST_THREADS / (n / 8); }
     static int band_planes(int n) { return (n - 1) / 3 + 1; }  // FusedGeom<n>::NB2
     template <int N, class SS, int KIND> static bool go(const FusedArgs& a, cudaStream_t st, bool set_attr) {
-        if (set_attr) return raise_smem_limit(k_fused_stage<SS, N, KIND>, FusedGeom<N>::smem(KIND));
+        if (set_attr) {
+            if (!raise_smem_limit(k_fused_stage<SS, N, KIND>, FusedGeom<N>::smem(KIND))) return false;
+            prefer_l1(k_fused_stage<SS, N, KIND>, FusedGeom<N>::smem(KIND), FUSED_BLOCKS);
+            return true;
+        }
         if (a.nb2 != FusedGeom<N>::NB2) return false;
         const size_t sm = FusedGeom<N>::smem(KIND);
         k_fused_stage<SS, N, KIND><<<persistent_grid(a.ntiles, FUSED_BLOCKS), FAST_THREADS, sm, st>>>(a);

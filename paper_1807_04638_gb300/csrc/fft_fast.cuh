@@ -194,8 +194,11 @@ template <int ALIGN> __device__ __forceinline__ unsigned char* align_smem(unsign
 
 // TWS: the twiddles are the per-stage tables in shared memory (else the
 // global table, read through the read-only cache); XA: exchange addressing
-// by XOR (MAP 1 lines of an XorEx<T, N>::ok plan on 8N-byte aligned tiles)
-template <class T, int N, int E, int TPL, int RADS, int S, int NS, int MAP, bool TWS = false, bool XA = false>
+// by XOR (MAP 1 lines of an XorEx<T, N>::ok plan on 8N-byte aligned tiles);
+// ONEX: every exchange uses one tile (b1 == b0), and a stage waits for the
+// line's loads of the previous exchange before it stores
+template <class T, int N, int E, int TPL, int RADS, int S, int NS, int MAP, bool TWS = false, bool XA = false,
+          bool ONEX = false>
 __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* b1, int c, int t, const cpx<T>* tw,
                                             int dir) {
     constexpr int R = (RADS >> (4 * S)) & 0xF;
@@ -205,6 +208,7 @@ __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* 
     static_assert(!XA || (MAP == 1 && XorEx<T, N>::ok), "XOR addressing needs the XOR layout of a power-of-two line");
     using SI = SIdx<T, N, MAP>;
     constexpr unsigned CB = (unsigned)sizeof(cpx<T>);
+    if constexpr (ONEX && S > 0 && !LAST) line_sync<MAP, TPL>();
     // XA: this line's base in the shared window
     unsigned lb = 0;
     if constexpr (XA) lb = (unsigned)__cvta_generic_to_shared(b0) + (unsigned)(c * SI::LP) * CB;
@@ -255,16 +259,16 @@ __device__ __forceinline__ void fast_stages(cpx<T> (&x)[E], cpx<T>* b0, cpx<T>* 
 #pragma unroll
             for (int m = 0; m < E; ++m) x[m] = b0[SI::at(c, t + TPL * m)];
         }
-        fast_stages<T, N, E, TPL, RADS, S + 1, NS * R, MAP, TWS, XA>(x, b1, b0, c, t, tw, dir);
+        fast_stages<T, N, E, TPL, RADS, S + 1, NS * R, MAP, TWS, XA, ONEX>(x, b1, b0, c, t, tw, dir);
     }
 }
 
-template <class T, int N, int MAP, bool TWS = false, bool XA = false>
+template <class T, int N, int MAP, bool TWS = false, bool XA = false, bool ONEX = false>
 __device__ __forceinline__ void fast_fft(cpx<T> (&x)[FastPlan<N>::E], cpx<T>* b0, cpx<T>* b1, int c, int t,
                                          const cpx<T>* tw, int dir) {
     constexpr int E = FastPlan<N>::E;
     line_sync<MAP, N / E>();  // the line's tiles may still be read by its previous transform
-    fast_stages<T, N, E, N / E, FastPlan<N>::RADS, 0, 1, MAP, TWS, XA>(x, b0, b1, c, t, tw, dir);
+    fast_stages<T, N, E, N / E, FastPlan<N>::RADS, 0, 1, MAP, TWS, XA, ONEX>(x, b0, b1, c, t, tw, dir);
 }
 
 // conj(Z_{N-k}) for element k = t + TPL m of a line transform held as the

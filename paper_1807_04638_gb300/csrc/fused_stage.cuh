@@ -73,8 +73,11 @@ template <int N> struct FusedGeom {
     static constexpr int NH = N / 2 + 1;
     static constexpr int SP = TL + 2;              // staged plane pitch (complex; 16-byte rows)
     static constexpr int XT = TL * SIdx<float, N, 1>::LP;  // one exchange tile
-    static constexpr int PH = (NH % 2 == 0) ? NH + 1 : NH;  // H pitch
-    static constexpr int HS = 2 * TL * PH;         // two unpacked outputs
+    // band planes of the dealiased grid: |k2| <= (N - 1) / 3 (the 2/3 rule of
+    // the projector P); the stages run only on dealiased grids
+    static constexpr int NB2 = (N - 1) / 3 + 1;
+    static constexpr int PH = (NB2 % 2 == 0) ? NB2 + 1 : NB2;  // H pitch (odd: conflict-free columns)
+    static constexpr int HS = 2 * TL * PH;         // two unpacked outputs (band planes)
     static constexpr int CPK = TL * 8 / 16;        // 16-byte chunks per staged plane
     // adjoint hand-off of two real fields: row pitch RP and field stride FS
     // (floats), both 16 banks apart modulo 32, so that neither the two rows
@@ -82,14 +85,12 @@ template <int N> struct FusedGeom {
     static constexpr int RP = N + 16;
     static constexpr int FS = TL * RP + 16;
     static constexpr int TWD = N + (NH + 1) / 2;   // twiddles, then kappa_2 (complex slots)
-    // band planes of the dealiased grid: |k2| <= (N - 1) / 3 (the 2/3 rule of
-    // the projector P); the stages run only on dealiased grids
-    static constexpr int NB2 = (N - 1) / 3 + 1;
     // Shared memory: two stage buffers, each the band planes k2 < NB2 of two
     // inputs and at least HS (the forward lines' unpacked outputs H live in
-    // the buffer that no copy targets then), two exchange tiles, the tables,
-    // and for the adjoint the hand-off rows.  Sized from NB2: what
-    // it leaves of the SM's 256 KB serves as L1 for the prefetched states.
+    // the buffer that no copy targets then), one exchange tile (shared by
+    // every exchange of a line transform), the tables, and for the adjoint
+    // the hand-off rows.  What it leaves of the SM's 256 KB serves as L1 for
+    // the prefetched states.
     // exchanges addressed by XOR (XorEx): every tile starts on a line-size
     // (8 N byte) boundary of the shared window
     static constexpr bool XA = XorEx<float, N>::ok;
@@ -97,7 +98,7 @@ template <int N> struct FusedGeom {
     static constexpr int STG0 = 2 * NB2 * SP > HS ? 2 * NB2 * SP : HS;
     static constexpr int STG = XA ? (STG0 + N - 1) / N * N : STG0;
     static constexpr size_t smem(int kind) {
-        return (size_t)(XAL - 16) + (size_t)(2 * STG + 2 * XT + TWD) * sizeof(cpx<float>) +
+        return (size_t)(XAL - 16) + (size_t)(2 * STG + XT + TWD) * sizeof(cpx<float>) +
                (kind == 1 ? (size_t)2 * FS * sizeof(float) : 0);
     }
     static_assert(TL % 2 == 0, "the adjoint pairs the rows of a tile");
@@ -338,8 +339,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
     constexpr bool XA = G::XA;
     cpx<float>* const stage0 = (cpx<float>*)align_smem<G::XAL>(smem_raw);  // buffers stage0 + sb * STG, sb < NBUF
     cpx<float>* const b0 = stage0 + NBUF * STG;
-    cpx<float>* const b1 = b0 + G::XT;
-    cpx<float>* const tws = b1 + G::XT;                 // twiddles
+    cpx<float>* const tws = b0 + G::XT;                 // twiddles
     float* const dks = (float*)(tws + N);              // kappa_2 (Nyquist zeroed)
     float* const R = (float*)(tws + G::TWD);           // adjoint: two real fields of the tile's rows
     const int c = threadIdx.x / TPL, t = threadIdx.x % TPL;
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                     x[m] = h.pack(mk(uv.x, uv.y), mk(uv.z, uv.w));
                 }
             }
-            fast_fft<float, N, 1, true, XA>(x, b0, b1, c, t, tws, +1);
+            fast_fft<float, N, 1, true, XA, true>(x, b0, b0, c, t, tws, +1);
             if constexpr (KIND == 0) {
                 switch (l) {
 #define LDDMM_TC(L) \
@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(FAST_THREADS, FUSED_BLOCKS) k_fused_stage(cons
                     for (int m = 0; m < E; ++m) x[m] = mk(Rq[TPL * m], Rq[RP + TPL * m]);
                 }
             }
-            fast_fft<float, N, 1, true, XA>(x, b0, b1, c, t, tws, -1);
+            fast_fft<float, N, 1, true, XA, true>(x, b0, b0, c, t, tws, -1);
             // every warp is done with the previous line's outputs in H
             __syncthreads();
             // unpack the two real rows' spectra: Z_k is register m of lane t
