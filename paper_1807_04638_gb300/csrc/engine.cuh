@@ -821,7 +821,8 @@ class Engine : public EngineBase {
             sc.sym[0] = to_symt<T>(sym(1.0, 0, -1, 1));
             {
                 PScope ps_(this, KC_SPEC, 2.0 * d.NS * sizeof(C));
-                k_spec_comb<T><<<pw_grid(d.NS), PW_THREADS, 0, st>>>(sc, tabs, d.n0, d.n1, d.n2h, out + c * d.NS);
+                k_spec_comb<T><<<spec_comb_blocks(d.n0, d.n2h), spec_comb_threads(d.n1), 0, st>>>(sc, tabs, d.n0, d.n1,
+                                                                                               d.n2h, out + c * d.NS);
             }
         }
     }
@@ -1638,7 +1639,8 @@ class Engine : public EngineBase {
             }
             {
                 PScope ps_(this, KC_SPEC, (double)(sc.nin + 1) * d.NS * sizeof(C));
-                k_spec_comb<T><<<pw_grid(d.NS), PW_THREADS, 0, st>>>(sc, tabs, d.n0, d.n1, d.n2h, tmp + c * d.NS);
+                k_spec_comb<T><<<spec_comb_blocks(d.n0, d.n2h), spec_comb_threads(d.n1), 0, st>>>(sc, tabs, d.n0, d.n1,
+                                                                                               d.n2h, tmp + c * d.NS);
             }
         }
         inv_vec(tmp, out);

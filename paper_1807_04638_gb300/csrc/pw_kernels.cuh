@@ -714,17 +714,24 @@ template <class T> struct SpecComb {
     SymT<T> sym[MAXI];
     int nin;
 };
+// A block walks (k2, k0) rows of n1 entries; its threads take the k1 of a
+// row, so that the frequency indices cost one division per row.
 template <class T>
 __global__ void k_spec_comb(SpecComb<T> sc, SpecTabs<T> tb, int n0, int n1, int n2h, cpx<T>* __restrict__ out) {
-    const size_t NS = (size_t)n0 * n1 * n2h;
-    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < NS; x += (size_t)gridDim.x * blockDim.x) {
-        const int k1 = (int)(x % n1);
-        const int k0 = (int)((x / n1) % n0);
-        const int k2 = (int)(x / ((size_t)n1 * n0));
-        cpx<T> acc = mk((T)0, (T)0);
-        for (int b = 0; b < sc.nin; ++b) acc = acc + sym_apply(sc.sym[b], tb, k0, k1, k2, sc.in[b][x]);
-        out[x] = acc;
+    const int rows = n0 * n2h;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int k2 = r / n0, k0 = r - k2 * n0;
+        const size_t base = (size_t)r * n1;
+        for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) {
+            const size_t x = base + k1;
+            cpx<T> acc = mk((T)0, (T)0);
+            for (int b = 0; b < sc.nin; ++b) acc = acc + sym_apply(sc.sym[b], tb, k0, k1, k2, sc.in[b][x]);
+            out[x] = acc;
+        }
     }
 }
+// launch shape of k_spec_comb: threads per block (whole warps covering a row, at most 256), blocks
+inline int spec_comb_threads(int n1) { return n1 >= 256 ? 256 : ((n1 + 31) / 32) * 32; }
+inline int spec_comb_blocks(int n0, int n2h) { return n0 * n2h < 152 * 16 ? n0 * n2h : 152 * 16; }
 
 }  // namespace lddmm
