@@ -125,6 +125,32 @@ def test_gradient_and_hessvec(pkg, prec, space, n):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_gradient_and_hessvec_rows_wider_than_a_block(pkg, prec):
+    """Spectral rows of 288 entries along k1 (2^5 3^2, a runtime-radix axis),
+    more than the 256 threads with which the spectral combination kernel
+    walks a row, so that its threads take several entries of a row."""
+    dtype, _ = DT[prec]
+    n = (8, 288, 16)
+    nt = 3
+    g, I0, I1, vtrue = problem(n, 11, nt)
+    p = O.Params(nt=nt)
+    v0 = 0.5 * vtrue
+    gl2, E, data, reg, tr = O.gradient(g, p, v0, I0, I1)
+    d = synth.band_limited_field(n, synth.rng_for(12), 3.0, 3) * g.h[0]
+    hl2 = O.hessvec(g, p, tr, d)
+    tol = F64_TOL if prec == "f64" else 1e-5
+    with pkg.Handle(n, params(pkg, prec, nt=nt)) as h:
+        grad = h.new_vec()
+        e = h.lddmm_gradient(dev(v0, dtype), dev(I0, dtype), dev(I1, dtype), grad)
+        hv = h.new_vec()
+        h.lddmm_hessvec(dev(d, dtype), hv)
+        h.lddmm_synchronize()
+    assert abs(e[0] - E) < tol * abs(E)
+    assert rel(host(grad), O.to_space(g, p, gl2)) < tol
+    assert rel(host(hv), O.to_space(g, p, hl2)) < tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_jacobi_sweeps_and_dot_test(pkg, prec):
     dtype, _ = DT[prec]
     n = (20, 12, 18)

@@ -1,4 +1,5 @@
-"""The no-allocation metric entry point agrees with the handle's metric apply.
+"""The no-allocation metric entry point agrees with the handle's metric apply
+and with the FP64 oracle.
 
 lddmm_apply_metric_noalloc serves callers that cannot allocate device memory
 (graph capture, real-time loops, plug-ins whose host owns all allocations):
@@ -50,6 +51,13 @@ def test_noalloc_matches_handle_two_calls_in_a_row(pkg, dtype, tol):
     torch.cuda.synchronize()
     assert rel(out_a, ref_a) < tol
     assert rel(out_b, ref_b) < tol
+    # and directly against the FP64 oracle: K = L^-1 and L^2
+    from oracle import lddmm_oracle as O
+    go = O.Grid(n, alpha=alpha, s=s)
+    want_a = torch.from_numpy(go.K(xa.double().cpu().numpy()))
+    want_b = torch.from_numpy(go.L(go.L(xb.double().cpu().numpy())))
+    assert rel(out_a.double().cpu(), want_a) < tol
+    assert rel(out_b.double().cpu(), want_b) < tol
     # in place (out == in) gives the same result
     xc = xa.clone()
     pkg.apply_metric_noalloc(xc, xc, -1, alpha, s)
