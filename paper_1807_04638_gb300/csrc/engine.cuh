@@ -328,7 +328,11 @@ template <class T> struct FastPass {
             k_fast_axis2<T, N><<<dim3(gx, nj), FAST_THREADS, sm, st>>>(pp);
         } else if (axis == 1) {
             const size_t sm = fast_c2c_smem<T, N>(1);
-            if (set_attr) return raise_smem_limit(k_fast_c2c<T, N, 1>, sm);
+            if (set_attr) {
+                if (!raise_smem_limit(k_fast_c2c<T, N, 1>, sm)) return false;
+                prefer_l1(k_fast_c2c<T, N, 1>, sm, FastOccC2C<T, N>::value);
+                return true;
+            }
             (void)n2h;
             const int ntiles = (int)(((size_t)pp.nb2 * n0 + TL - 1) / TL);
             pp.fd_tiles = FastDiv((unsigned)ntiles);
@@ -336,7 +340,11 @@ template <class T> struct FastPass {
             k_fast_c2c<T, N, 1><<<persistent_grid(ntiles * nj), FAST_THREADS, sm, st>>>(pp, ntiles);
         } else {
             const size_t sm = fast_c2c_smem<T, N>(0);
-            if (set_attr) return raise_smem_limit(k_fast_c2c<T, N, 0>, sm);
+            if (set_attr) {
+                if (!raise_smem_limit(k_fast_c2c<T, N, 0>, sm)) return false;
+                prefer_l1(k_fast_c2c<T, N, 0>, sm, FastOccC2C<T, N>::value);
+                return true;
+            }
             const int tpk = (pp.c1 + TL - 1) / TL + (n1 - pp.s1 + TL - 1) / TL;
             const int ntiles = pp.nb2 * tpk;
             pp.fd_tiles = FastDiv((unsigned)ntiles);

@@ -391,12 +391,26 @@ __device__ __forceinline__ void sym_line(const SymT<T>& sy, const SpecTabs<T>& t
 // current one is transformed, so DRAM latency overlaps the butterflies.
 //   AXIS 1: a tile is TL consecutive contiguous lines along k1 ([line][N]).
 //   AXIS 0: a tile is TL consecutive k1 columns of lines along k0 ([row][TL]).
+//   Exchange tiles: axis 1 (its line's threads in one warp) uses one tile for
+//   every exchange.  Axis 0 alternates between two tiles (exchange j in
+//   tile j mod 2); with an odd number of stages (3, 5, ...) the last exchange
+//   is in tile 1, so every read of tile 0 ends before the block barrier of a
+//   later exchange, and tile 0 can be the stage buffer of the unit being
+//   transformed (its tile is in registers by then): no copy refills it
+//   before that barrier.  The rest of the SM's storage stays L1 for the bases.
 template <class T, int N, int AXIS> struct C2CGeom {
     static constexpr int E = FastPlan<N>::E;
     static constexpr int TPL = N / E;
     static constexpr int TL = FAST_THREADS / TPL;
     static constexpr int MAP = AXIS == 1 ? 1 : 0;
     static constexpr int TILE = TL * N;  // complex elements of one staged tile
+    static constexpr int XT = TL * SIdx<T, N, MAP>::LP;  // one exchange tile
+    static constexpr bool ALIAS = AXIS == 0 && TwTable<N>::nstages() >= 3 && TwTable<N>::nstages() % 2 == 1;
+    static constexpr int SB = ALIAS && XT > TILE ? XT : TILE;  // one stage buffer
+    static constexpr size_t smem() {
+        return ((size_t)2 * SB + (size_t)(AXIS == 1 || ALIAS ? 1 : 2) * XT + (size_t)N) * sizeof(cpx<T>) +
+               (size_t)2 * N * sizeof(T);  // + twiddles, kappa^2 and derivative tables of the axis
+    }
 };
 
 template <class T, int N, int AXIS>
@@ -407,11 +421,10 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
     // the two stage buffers: stage0 + sb * TILE (pointer arithmetic, not an
     // indexed array, which would live in local memory)
     cpx<T>* const stage0 = (cpx<T>*)smem_raw;
-    cpx<T>* b0 = stage0 + 2 * G::TILE;
-    cpx<T>* b1 = b0 + TL * SIdx<T, N, MAP>::LP;
+    cpx<T>* const xt = stage0 + 2 * G::SB;  // exchange tile(s)
     // the axis' twiddles and symbol tables in shared memory (the first
     // barrier of the main loop orders these stores before their reads)
-    cpx<T>* const tws = b1 + TL * SIdx<T, N, MAP>::LP;
+    cpx<T>* const tws = xt + (AXIS == 1 || G::ALIAS ? 1 : 2) * G::XT;
     T* const ksqs = (T*)(tws + N);
     T* const dks = ksqs + N;
     static_assert(TwTable<N>::SIZE <= N, "per-stage twiddle tables fit N entries");
@@ -479,7 +492,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
                 for (int i = threadIdx.x; i < chunks; i += FAST_THREADS) {
                     // c1, s1 are even: a 16-byte chunk lies wholly inside or outside the band
                     if (skip && k1_out((16 * i / (int)sizeof(cpx<T>)) % N)) continue;
-                    cp_async16((char*)(stage0 + sb * G::TILE) + 16 * i, (const char*)(src + g0) + 16 * i);
+                    cp_async16((char*)(stage0 + sb * G::SB) + 16 * i, (const char*)(src + g0) + 16 * i);
                 }
             } else {
                 // 16-byte chunks per row: CPR for a full tile (compile time), cpr valid
@@ -488,7 +501,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
                 for (int i = threadIdx.x; i < N * CPR; i += FAST_THREADS) {
                     const int p = i / CPR, ch = i % CPR;
                     if (ch < cpr)
-                        cp_async16((char*)((stage0 + sb * G::TILE) + p * TL) + 16 * ch,
+                        cp_async16((char*)((stage0 + sb * G::SB) + p * TL) + 16 * ch,
                                    (const char*)(src + g0 + p * n1) + 16 * ch);
                 }
             }
@@ -521,7 +534,10 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
         int g0, nval, k2t, kb;
         tile_geo(tl, g0, nval, k2t, kb);
         const bool valid = c < nval;
-        const cpx<T>* tile = (stage0 + sb * G::TILE);
+        const cpx<T>* tile = (stage0 + sb * G::SB);
+        // this unit's exchange tiles
+        cpx<T>* const b0 = AXIS == 1 ? xt : (G::ALIAS ? stage0 + sb * G::SB : xt);
+        cpx<T>* const b1 = AXIS == 1 ? xt : (G::ALIAS ? xt : xt + G::XT);
         // frequency indices of the other two axes for this thread's line
         int k0b, k1b, k2b;
         if (AXIS == 1) {
@@ -553,7 +569,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
 #pragma unroll
                     for (int m = 0; m < E; ++m) x[m] = acc[m];
                     sym_line<T, AXIS, E, TPL>(sy, pp.tabs, ksqs, dks, AXIS == 0 ? k1b : k0b, k2b, t, x);
-                    fast_fft<T, N, MAP, true>(x, b0, b1, c, t, tws, +1);
+                    fast_fft<T, N, MAP, true, false, AXIS == 1>(x, b0, b1, c, t, tws, +1);
                     if (valid) {
                         cpx<T>* ob = (cpx<T>*)job.out[o] + gidx(t);
                         const int sm = AXIS == 1 ? TPL : TPL * n1;  // element step between m
@@ -577,7 +593,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
 #pragma unroll
             for (int m = 0; m < E; ++m) x[m] = valid ? tile[at(t + TPL * m)] : mk((T)0, (T)0);
             __syncthreads();
-            fast_fft<T, N, MAP, true>(x, b0, b1, c, t, tws, -1);
+            fast_fft<T, N, MAP, true, false, AXIS == 1>(x, b0, b1, c, t, tws, -1);
             const SymT<T> sy = job.isym[q];
 sym_line<T, AXIS, E, TPL>(sy, pp.tabs, ksqs, dks, AXIS == 0 ? k1b : k0b, k2b, t, x);
 #pragma unroll
@@ -914,10 +930,7 @@ template <class T, int N> constexpr size_t fast_axis2p_smem() {
 }
 
 template <class T, int N> constexpr size_t fast_c2c_smem(int axis) {
-    return ((size_t)2 * C2CGeom<T, N, 1>::TILE +
-            (size_t)2 * (FAST_THREADS / (N / FastPlan<N>::E)) * (axis == 1 ? SIdx<T, N, 1>::LP : SIdx<T, N, 0>::LP) +
-            (size_t)N) * sizeof(cpx<T>) +
-           (size_t)2 * N * sizeof(T);  // twiddles, kappa^2 and derivative tables of the axis
+    return axis == 1 ? C2CGeom<T, N, 1>::smem() : C2CGeom<T, N, 0>::smem();
 }
 template <class T, int N> constexpr size_t fast_axis2_smem() {
     constexpr int TL = FAST_THREADS / (N / FastPlan<N>::E);
