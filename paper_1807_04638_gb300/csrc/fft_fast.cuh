@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (FastOccC2C<T, N>::value)) k_fas
     using G = C2CGeom<T, N, AXIS>;
     constexpr int E = G::E, TPL = G::TPL, TL = G::TL, MAP = G::MAP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // the two stage buffers: stage0 + sb * TILE (pointer arithmetic, not an
+    // the two stage buffers: stage0 + sb * SB (pointer arithmetic, not an
     // indexed array, which would live in local memory)
     cpx<T>* const stage0 = (cpx<T>*)smem_raw;
     cpx<T>* const xt = stage0 + 2 * G::SB;  // exchange tile(s)
