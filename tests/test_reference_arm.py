@@ -19,3 +19,14 @@ def test_reference_arm_prints_one_json_line():
     assert d["unit"] == "Hv/s" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "Hv/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_stored_stage_traffic_belongs_to_the_current_kernel_sources():
+    """bench.py reports the ncu DRAM bytes of the stage kernels only for the
+    kernel sources they were measured on; the stored entry must name the
+    digest of the committed sources, or the line's roofline.traffic is null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.TRAFFIC["digest"] == bench.kernel_digest()
+    for k in ("tangent_stage_fused", "adjoint_stage_fused"):
+        assert 1e8 < bench.TRAFFIC[k] < 1e9
